@@ -1,0 +1,309 @@
+"""Plain FP64 CPU oracle of the enhanced shifted-Laplace rational filter (ParaSLRF).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this module.  It shares no code with the CUDA
+library and is deliberately slow and literal: numpy/scipy in float64/complex128, each
+function following one step of the method in the paper's order.
+
+Sources (arXiv 2510.17334):
+  * rational filter Phi(lambda) = sum_j w_j/(lambda - sigma_j)         -- Sec. 2, eq. (3)
+  * conjugate poles sigma_{N+j} = conj(sigma_j), w_{N+j} = conj(w_j);
+    filtered block U = sum_j 2 Re(w_j Y_j)                              -- Sec. 2, Alg. 1
+  * shifted systems (A - sigma_j B) Y = B V                             -- Sec. 1, eq. (2)
+  * poles on the lines y = x(1 +- alpha i), alpha = 1, beta = 0.01      -- Sec. 2.2, Sec. 3.2
+  * enhanced method: locking, B-orthogonalisation against locked X,
+    warm start Y_init = v/(theta - sigma), fixed It_max                  -- Sec. 4, Alg. 2
+  * Cayley equivalence of the warm start                                -- Sec. 4, Proposition
+  * eigen-residual stopping test, inner tolerance 1e-10                 -- Sec. 3.2
+
+Readings where the paper is silent (each listed in the design notes):
+  * pole/weight design: sigma_j = gamma x_j (1 + alpha i), x_j = (j - 1/2)/m; weights
+    minimise sum_t (Phi(t) - 1[t <= gamma])^2 + beta ||w/gamma||^2 over 3000 uniform
+    samples on (0, gamma] and 3000 geometric samples on [1.3 gamma, 51 gamma]
+    (beta read as a Tikhonov weight; the band (gamma, 1.3 gamma) is not fitted).
+  * inner solver: COCG (unconjugated bilinear form), stop per column at
+    ||r||/||r0|| <= tol_in or It_max updates (r0 the warm-started initial residual,
+    i.e. the Cayley system's own right-hand side by the Proposition).
+  * locking test: ||A v - theta B v|| / ||A v|| <= tol_eig and 0 < theta <= gamma.
+  * orthogonalisation: CGS2 in the B-inner product; B-orthonormalisation: Cholesky-QR2;
+    Rayleigh-Ritz on the standard problem U^T A U (U B-orthonormal).
+  * stopping: no active Ritz value <= gamma left after locking, two outer steps in a row.
+  * start block: standard Gaussian (PCG64); first-step initial guess y0 = 0.
+  * eigenvector sign: the entry of largest magnitude is made positive.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+# status codes mirrored by the library's documented semantics (not shared code)
+OK = 0
+E_CHOL = -6
+E_NOCONV = -7
+
+
+# ----------------------------------------------------------------------------------------
+# a1: poles and weights (Sec. 2.2; reading R1)
+# ----------------------------------------------------------------------------------------
+def slrf_poles(m: int, gamma: float, alpha: float = 1.0, beta: float = 0.01, band: float = 1.3,
+               n_in: int = 3000, n_out: int = 3000, t_max: float = 51.0):
+    """Upper-half-plane poles sigma_j and weights w_j (j = 1..m) of the SLRF filter.
+
+    Poles lie on the line Im = alpha * Re (Sec. 2.2, sigma = Re(sigma)(1 + alpha i)).
+    Weights are the Tikhonov-regularised least-squares fit of the interval indicator.
+    Everything is designed on the normalised axis t/gamma and then scaled by gamma.
+    """
+    x = (np.arange(1, m + 1) - 0.5) / m
+    sig_hat = x * (1.0 + 1j * alpha)
+    t_in = (np.arange(n_in) + 0.5) / n_in
+    t_out = np.geomspace(band, t_max, n_out)
+    t = np.concatenate([t_in, t_out])
+    f = np.concatenate([np.ones(n_in), np.zeros(n_out)])
+    C = 1.0 / (t[:, None] - sig_hat[None, :])
+    # Phi(t) = sum_j 2 Re(w_j C_j(t)) = sum_j 2 (Re w_j Re C_j - Im w_j Im C_j)
+    G = np.hstack([2.0 * C.real, -2.0 * C.imag])
+    lhs = G.T @ G + beta * np.eye(2 * m)
+    rhs = G.T @ f
+    u = np.linalg.solve(lhs, rhs)
+    w_hat = u[:m] + 1j * u[m:]
+    return gamma * sig_hat, gamma * w_hat
+
+
+def filter_value(t, sigma, w):
+    """Phi(t) for real t with the conjugate half implied: sum_j 2 Re(w_j / (t - sigma_j))."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.sum(2.0 * np.real(w[None, :] / (t.reshape(-1, 1) - sigma[None, :])), axis=1).reshape(t.shape)
+
+
+# ----------------------------------------------------------------------------------------
+# a3/a4: COCG on (A - sigma B) y = b, columns independent
+# ----------------------------------------------------------------------------------------
+@dataclass
+class CocgInfo:
+    iters: np.ndarray  # updates performed per column
+    relres: np.ndarray  # final recurrence ||r|| / ||b||
+    breakdown: np.ndarray  # bool per column
+
+
+def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarray,
+         it_max: int, tol: float):
+    """Conjugate orthogonal CG for the complex-symmetric M = A - sigma B, one RHS per column.
+
+    ``sigma`` is a scalar or one shift per column (columns are independent systems).
+    Textbook COCG (van der Vorst & Melissen): CG with the unconjugated form x^T y.
+      r = b - M y0, p = r, rho = r^T r
+      repeat: q = M p; mu = p^T q; alpha = rho/mu; y += alpha p; r -= alpha q;
+              stop if ||r|| <= tol ||r0|| or It_max updates; rho' = r^T r;
+              beta = rho'/rho; p = r + beta p.
+    The tolerance is relative to the initial residual r0 = b - M y0.  With the warm start
+    y0 = v/(theta - sigma) this is the relative residual of the equivalent Cayley system
+    (A - sigma B) u = (A - theta B) v solved from u0 = 0 (Sec. 4, Proposition (i)); with
+    y0 = 0 it is the usual ||r||/||b||.
+    A column whose mu or rho vanishes (or is not finite) stops and is flagged.
+    """
+    sig = np.broadcast_to(np.asarray(sigma, dtype=np.complex128), (b.shape[1],))
+
+    def M(X):
+        return (A @ X) - (B @ X) * sig[None, :]
+
+    y = y0.astype(np.complex128, copy=True)
+    r = b.astype(np.complex128) - M(y)
+    rn = np.linalg.norm(r, axis=0)
+    bn = rn.copy()  # ||r0||
+    active = rn > 0
+    iters = np.zeros(b.shape[1], dtype=np.int64)
+    brk = np.zeros(b.shape[1], dtype=bool)
+    p = r.copy()
+    rho = np.sum(r * r, axis=0)
+    for _ in range(it_max):
+        if not active.any():
+            break
+        q = M(p)
+        mu = np.sum(p * q, axis=0)
+        bad = active & ((mu == 0) | ~np.isfinite(mu))
+        brk |= bad
+        active &= ~bad
+        alpha = np.where(active, rho / np.where(mu == 0, 1, mu), 0)
+        y += alpha[None, :] * p
+        r -= alpha[None, :] * q
+        iters += active
+        rn = np.linalg.norm(r, axis=0)
+        active &= ~(rn <= tol * bn)
+        rho_new = np.sum(r * r, axis=0)
+        bad = active & ((rho == 0) | ~np.isfinite(rho_new))
+        brk |= bad
+        active &= ~bad
+        beta = np.where(active, rho_new / np.where(rho == 0, 1, rho), 0)
+        rho = rho_new
+        p = r + beta[None, :] * p
+    relres = np.where(bn > 0, rn / np.where(bn > 0, bn, 1), 0.0)  # ||r|| / ||r0||
+    return y, CocgInfo(iters, relres, brk)
+
+
+# ----------------------------------------------------------------------------------------
+# a2-a5: filter apply  U = sum_j 2 Re(w_j Y_j),  (A - sigma_j B) Y_j = B V
+# ----------------------------------------------------------------------------------------
+@dataclass
+class FilterInfo:
+    iters: np.ndarray  # (m, k)
+    relres: np.ndarray  # (m, k)
+    breakdown: np.ndarray  # (m, k)
+
+
+def filter_apply(A, B, V, theta, sigma, w, it_max, tol):
+    """Apply the rational filter to the real block V (n x k), Alg. 2 lines 7-14.
+
+    ``theta`` = None gives the zero initial guess; otherwise column c starts from
+    y0 = v_c / (theta_c - sigma_j) (Alg. 2 line 21).  All m x k systems are solved
+    side by side as independent columns, pole-major: column j*k + c is pole j, vector c.
+    """
+    n, k = V.shape
+    m = len(sigma)
+    b = B @ V
+    bb = np.tile(b, (1, m))
+    sig_cols = np.repeat(np.asarray(sigma), k)
+    if theta is None:
+        y0 = np.zeros((n, m * k), dtype=np.complex128)
+    else:
+        th = np.tile(np.asarray(theta, dtype=np.float64), m)
+        y0 = np.tile(V, (1, m)) / (th[None, :] - sig_cols[None, :])
+    Y, info = cocg(A, B, sig_cols, bb, y0, it_max, tol)
+    U = np.zeros((n, k))
+    for j in range(m):
+        U += 2.0 * np.real(w[j] * Y[:, j * k:(j + 1) * k])
+    return U, FilterInfo(info.iters.reshape(m, k), info.relres.reshape(m, k),
+                         info.breakdown.reshape(m, k))
+
+
+# ----------------------------------------------------------------------------------------
+# a6: B-orthogonalise against the locked vectors (Alg. 2 lines 15-17), CGS2
+# ----------------------------------------------------------------------------------------
+def b_orth(U, X, BX):
+    """U <- U - X (X^T B U), twice, using the stored B X."""
+    for _ in range(2):
+        U = U - X @ (BX.T @ U)
+    return U
+
+
+# ----------------------------------------------------------------------------------------
+# a7: Cholesky-QR2 in the B-inner product
+# ----------------------------------------------------------------------------------------
+def cholqr2(U, B):
+    """Two passes of G = U^T B U, G = R^T R, U <- U R^{-1}.  Returns (U, status)."""
+    for _ in range(2):
+        G = U.T @ (B @ U)
+        try:
+            Lc = np.linalg.cholesky(G)
+        except np.linalg.LinAlgError:
+            return U, E_CHOL
+        R = Lc.T
+        U = sla.solve_triangular(R, U.T, trans="T", lower=False).T
+    return U, OK
+
+
+# ----------------------------------------------------------------------------------------
+# a8: Rayleigh-Ritz on the B-orthonormal basis (Alg. 2 line 18)
+# ----------------------------------------------------------------------------------------
+def rayleigh_ritz(U, A):
+    """theta ascending and V = U S from the eigenpairs of H = U^T A U."""
+    H = U.T @ (A @ U)
+    theta, S = np.linalg.eigh(H)
+    V = U @ S
+    return theta, V
+
+
+def sign_normalise(V):
+    """Flip each column so that its entry of largest magnitude is positive."""
+    idx = np.argmax(np.abs(V), axis=0)
+    s = np.sign(V[idx, np.arange(V.shape[1])])
+    s[s == 0] = 1
+    return V * s[None, :]
+
+
+# ----------------------------------------------------------------------------------------
+# a9: residuals, convergence, locking
+# ----------------------------------------------------------------------------------------
+def ritz_residuals(A, B, V, theta):
+    """Relative residual ||A v - theta B v||_2 / ||A v||_2 per column, and the paper's
+    form ||(A - theta B) v||_2 / (theta ||v||_B) (Sec. 3.2)."""
+    AV = A @ V
+    BV = B @ V
+    R = AV - BV * theta[None, :]
+    rn = np.linalg.norm(R, axis=0)
+    res = rn / np.linalg.norm(AV, axis=0)
+    vb = np.sqrt(np.sum(V * BV, axis=0))
+    res_paper = rn / (np.abs(theta) * vb)
+    return res, res_paper, BV
+
+
+@dataclass
+class SolveResult:
+    status: int
+    evals: np.ndarray
+    X: np.ndarray
+    resid: np.ndarray
+    outer_iters: int
+    trace: list = field(default_factory=list)
+
+
+def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, outer_max=100,
+                  alpha=1.0, beta=0.01, lock=True, warm=True, poles=None, keep_trace=False):
+    """Enhanced ParaSLRF, Alg. 2, on one address space.
+
+    Returns the locked eigenpairs sorted ascending.  ``lock`` = False / ``warm`` = False
+    give the basic method of Alg. 1 (no locking, zero initial guesses).
+    """
+    A = sp.csr_matrix(A)
+    B = sp.csr_matrix(B)
+    n, L = V1.shape
+    sigma, w = slrf_poles(m, gamma, alpha, beta) if poles is None else poles
+    V = np.array(V1, dtype=np.float64)
+    theta = None
+    X = np.zeros((n, 0))
+    BX = np.zeros((n, 0))
+    Theta = np.zeros(0)
+    Res = np.zeros(0)
+    quiet = 0
+    trace = []
+    status = E_NOCONV
+    k = 0
+    for k in range(1, outer_max + 1):
+        U, finfo = filter_apply(A, B, V, theta if warm else None, sigma, w, it_max, tol_in)
+        if X.shape[1] > 0:
+            U = b_orth(U, X, BX)
+        U, st = cholqr2(U, B)
+        if st != OK:
+            status = st
+            break
+        th, V = rayleigh_ritz(U, A)
+        V = sign_normalise(V)
+        res, res_paper, BV = ritz_residuals(A, B, V, th)
+        conv = (res <= tol_eig) & (th > 0) & (th <= gamma)
+        if keep_trace:
+            trace.append(dict(k=k, n_act=V.shape[1], theta=th.copy(), res=res.copy(),
+                              n_lock=int(conv.sum()), inner_iters=finfo.iters.copy()))
+        if lock:
+            X = np.hstack([X, V[:, conv]])
+            BX = np.hstack([BX, BV[:, conv]])
+            Theta = np.concatenate([Theta, th[conv]])
+            Res = np.concatenate([Res, res[conv]])
+            V = V[:, ~conv]
+            theta = th[~conv]
+            pending = np.any(theta <= gamma)
+        else:
+            # Alg. 1: nothing is locked; the wanted Ritz pairs are the result once all converge
+            want = (th > 0) & (th <= gamma)
+            pending = not np.all(conv[want]) or not want.any()
+            Xout, Theta, Res = V[:, want], th[want], res[want]
+            theta = th
+        quiet = 0 if pending else quiet + 1
+        if quiet >= 2:
+            status = OK
+            break
+    if not lock:
+        X = Xout
+    order = np.argsort(Theta, kind="stable")
+    return SolveResult(status, Theta[order], X[:, order], Res[order], k, trace)

@@ -1,0 +1,259 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each check is independent of the oracle's own code: closed-form FEM spectra, dense
+library eigensolvers and solvers, Sylvester inertia, the Proposition of Sec. 4, CG from
+scipy, and invariants (B-orthonormality, conjugate symmetry, filter on eigenvectors).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import slrf_inputs as si
+from oracle import slrf_oracle as orc
+import pins
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _small_q1(nodes=(6, 5, 4), shift=1e-3):
+    p = si.q1_scalar(nodes, shift=shift)
+    return p, p.A(), p.B()
+
+
+# ---------------------------------------------------------------- a1: poles and weights
+def test_poles_on_shifted_laplace_line():
+    """Sec. 2.2: sigma = Re(sigma) (1 + alpha i); real parts inside (0, gamma)."""
+    for alpha in (1.0, 0.5):
+        s, w = orc.slrf_poles(8, 250.0, alpha=alpha)
+        assert np.allclose(s.imag, alpha * s.real, rtol=0, atol=1e-12)
+        assert np.all((s.real > 0) & (s.real < 250.0))
+        assert len(np.unique(s)) == 8
+
+
+def test_pole_weights_solve_the_regularised_fit():
+    """The weights equal an SVD least-squares solve of the stacked system [G; sqrt(beta) I]."""
+    m, beta = 8, 0.01
+    s, w = orc.slrf_poles(m, 1.0, beta=beta)
+    x = (np.arange(1, m + 1) - 0.5) / m
+    assert np.allclose(s, x * (1 + 1j))
+    t = np.concatenate([(np.arange(3000) + 0.5) / 3000, np.geomspace(1.3, 51.0, 3000)])
+    f = np.concatenate([np.ones(3000), np.zeros(3000)])
+    # Phi(t) = sum_j w_j/(t - s_j) + conj(w_j)/(t - conj(s_j)) written as a real design
+    cols = []
+    for j in range(m):
+        e = np.zeros(m, complex)
+        e[j] = 1.0
+        cols.append(sum(e[i] / (t - s[i]) + np.conj(e[i]) / (t - np.conj(s[i])) for i in range(m)).real)
+    for j in range(m):
+        e = np.zeros(m, complex)
+        e[j] = 1j
+        cols.append(sum(e[i] / (t - s[i]) + np.conj(e[i]) / (t - np.conj(s[i])) for i in range(m)).real)
+    G = np.stack(cols, axis=1)
+    Gs = np.vstack([G, np.sqrt(beta) * np.eye(2 * m)])
+    u, *_ = np.linalg.lstsq(Gs, np.concatenate([f, np.zeros(2 * m)]), rcond=None)
+    assert np.allclose(w, u[:m] + 1j * u[m:], rtol=1e-8, atol=1e-10)
+
+
+def test_filter_shape():
+    """Phi passes (0, gamma] and damps [1.3 gamma, inf): the filter property of Sec. 2."""
+    g = 4150.528
+    s, w = orc.slrf_poles(8, g)
+    inside = orc.filter_value(np.linspace(1e-3, 1, 500) * g, s, w)
+    outside = orc.filter_value(np.geomspace(1.3, 1e4, 500) * g, s, w)
+    assert inside.min() > 0.8 and inside.max() < 1.1
+    assert np.abs(outside).max() < 0.25
+    # the conjugate half: w/(t - s) + conj(w)/(t - conj s) = 2 Re(w/(t - s))
+    t = 0.37 * g
+    full = np.sum(w / (t - s) + np.conj(w) / (t - np.conj(s)))
+    assert abs(full.imag) < 1e-12 and abs(full.real - orc.filter_value(t, s, w)) < 1e-12
+
+
+# ---------------------------------------------------------------- a3/a4: COCG
+def test_cocg_equals_scipy_cg_for_a_real_shift():
+    """For a real shift sigma < 0, A - sigma B is SPD and COCG is CG: iterate k matches
+    scipy's CG stopped after k iterations."""
+    p, A, B = _small_q1()
+    rng = np.random.default_rng(0)
+    b = rng.standard_normal((p.n, 1))
+    M = (A + 2.0 * B).tocsr()
+    for k in (1, 3, 7):
+        y, info = orc.cocg(A, B, -2.0, b, np.zeros_like(b), k, 0.0)
+        x_ref, _ = spla.cg(M, b[:, 0], x0=np.zeros(p.n), rtol=0.0, atol=0.0, maxiter=k)
+        assert info.iters[0] == k
+        assert np.allclose(y[:, 0].real, x_ref, rtol=1e-10, atol=1e-12 * np.abs(x_ref).max())
+        assert np.abs(y.imag).max() == 0
+
+
+def test_cocg_solves_complex_symmetric_system():
+    """Converged COCG equals a dense complex solve of (A - sigma B) y = b."""
+    p, A, B = _small_q1((4, 4, 3))
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal((p.n, 3))
+    sig = 0.3 * 250 * (1 + 1j)
+    y, info = orc.cocg(A, B, sig, b, np.zeros((p.n, 3)), 400, 1e-13)
+    ref = np.linalg.solve(A.toarray() - sig * B.toarray(), b)
+    assert np.abs(y - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.all(info.relres <= 1e-13) and not info.breakdown.any()
+    # the conjugate pole gives the conjugate solution (Sec. 2: sigma_{N+j} = conj sigma_j)
+    yc, _ = orc.cocg(A, B, np.conj(sig), b, np.zeros((p.n, 3)), 400, 1e-13)
+    assert np.abs(yc - np.conj(y)).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_cocg_breakdown_is_flagged():
+    """A 2x2 complex-symmetric system with p^T M p = 0 on the first step stops, flagged."""
+    A = sp.csr_matrix(np.array([[1.0, 0.0], [0.0, -1.0]]))
+    B = sp.csr_matrix(np.eye(2))
+    b = np.array([[1.0], [1.0]])
+    # M = A - 0*B = diag(1, -1); p = b; p^T M p = 1 - 1 = 0
+    y, info = orc.cocg(A, B, 0.0, b, np.zeros((2, 1)), 10, 0.0)
+    assert info.breakdown[0] and info.iters[0] == 0 and np.all(y == 0)
+
+
+def test_proposition_initial_residual_and_krylov_space():
+    """Sec. 4, Proposition: with y0 = v/(theta - sigma), r0 = (A - theta B) v / (sigma - theta),
+    and the Cayley iterate u_k (from u0 = 0, rhs (A - theta B) v) satisfies
+    u_k = v + (sigma - theta) y_k at every step."""
+    p, A, B = _small_q1((5, 4, 4))
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((p.n, 1))
+    theta, sig = 37.0, 55.0 * (1 + 1j)
+    y0 = v / (theta - sig)
+    r0 = B @ v - (A @ y0 - sig * (B @ y0))
+    rc = A @ v - theta * (B @ v)
+    assert np.allclose(r0, rc / (sig - theta), rtol=1e-12, atol=1e-13 * np.abs(rc).max())
+    for k in (1, 4, 9):
+        y, _ = orc.cocg(A, B, sig, B @ v, y0, k, 0.0)
+        u, _ = orc.cocg(A, B, sig, rc, np.zeros_like(v), k, 0.0)
+        assert np.allclose(u, v + (sig - theta) * y, rtol=1e-9, atol=1e-10 * np.abs(u).max())
+
+
+# ---------------------------------------------------------------- a5: the filter on eigenvectors
+def test_filter_apply_on_exact_eigenvectors():
+    """With X exact eigenvectors and converged solves, filter_apply(X) = X diag(Phi(lambda))."""
+    p, A, B = _small_q1((5, 4, 3))
+    lam, X = sla.eigh(A.toarray(), B.toarray())
+    gamma = 0.5 * (lam[9] + lam[10])
+    s, w = orc.slrf_poles(8, gamma)
+    Xs = X[:, :14]
+    U, info = orc.filter_apply(A, B, Xs, None, s, w, 500, 1e-14)
+    ref = Xs * orc.filter_value(lam[:14], s, w)[None, :]
+    assert np.abs(U - ref).max() <= 1e-9 * np.abs(ref).max()
+    # same with the warm start from the exact eigenvalues: zero initial residual, no iterations
+    U2, info2 = orc.filter_apply(A, B, Xs, lam[:14], s, w, 500, 1e-14)
+    assert np.abs(U2 - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- a6-a8
+def test_borth_cholqr2_rayleigh_ritz():
+    p, A, B = _small_q1((6, 5, 4))
+    Bd = B.toarray()
+    lam, Xe = sla.eigh(A.toarray(), Bd)
+    rng = np.random.default_rng(3)
+    X = Xe[:, :5]
+    BX = B @ X
+    U0 = rng.standard_normal((p.n, 12))
+    U = orc.b_orth(U0, X, BX)
+    assert np.abs(X.T @ (B @ U)).max() <= 1e-12 * np.abs(U).max()
+    Q, st = orc.cholqr2(U, B)
+    assert st == orc.OK
+    assert np.abs(Q.T @ Bd @ Q - np.eye(12)).max() <= 1e-12
+    T = np.linalg.lstsq(U, Q, rcond=None)[0]  # Q = U T with T upper triangular
+    assert np.abs(np.tril(T, -1)).max() <= 1e-10 * np.abs(T).max()
+    # Rayleigh-Ritz on an exact invariant subspace returns the exact eigenvalues
+    Z, _ = orc.cholqr2(Xe[:, 3:11] @ rng.standard_normal((8, 8)), B)
+    th, V = orc.rayleigh_ritz(Z, A)
+    assert np.allclose(th, lam[3:11], rtol=1e-11)
+    assert np.abs(V.T @ Bd @ V - np.eye(8)).max() <= 1e-12
+    res, res_paper, _ = orc.ritz_residuals(A, B, V, th)
+    assert res.max() <= 1e-10 and res_paper.max() <= 1e-10
+
+
+def test_cholqr2_reports_a_non_spd_gram():
+    p, A, B = _small_q1((4, 4, 3))
+    U = np.ones((p.n, 3))  # rank one
+    _, st = orc.cholqr2(U, B)
+    assert st == orc.E_CHOL
+
+
+# ---------------------------------------------------------------- a9 / Alg. 2 end to end
+def test_solve_bar1d_closed_form_and_sturm_count():
+    """1D bar: every eigenvalue in (0, gamma] to 1e-10 of the closed form, the count equal
+    to the Sturm count of A - gamma B, residuals <= 1e-8, X B-orthonormal."""
+    n = 300
+    p = si.bar1d_pencil(n)
+    lam = pins.bar1d_eigs(n)
+    gamma = 0.5 * (lam[11] + lam[12])
+    h = 1.0 / (n + 1)
+    cnt = pins.sturm_count(np.full(n, 2 / h), np.full(n - 1, -1 / h), gamma,
+                           np.full(n, 4 * h / 6), np.full(n - 1, h / 6))
+    assert cnt == 12
+    V1 = si.start_block(n, 18, 11)
+    r = orc.enhanced_slrf(p.A(), p.B(), gamma, V1, m=8, it_max=60, outer_max=40)
+    assert r.status == orc.OK
+    assert len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-10
+    assert r.resid.max() <= 1e-8
+    assert np.abs(r.X.T @ (p.B() @ r.X) - np.eye(cnt)).max() <= 1e-10
+    # eigenvectors: sin(k pi x_i), compared up to sign through B-inner products
+    xg = np.arange(1, n + 1) * h
+    for k in range(cnt):
+        s = np.sin((k + 1) * np.pi * xg)
+        s /= np.sqrt(s @ (p.B() @ s))
+        assert abs(abs(s @ (p.B() @ r.X[:, k])) - 1.0) <= 1e-8
+
+
+def test_solve_q1_against_dense_eigh_and_inertia():
+    nodes = (6, 6, 5)
+    p, A, B = _small_q1(nodes)
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    closed = pins.q1_neumann_eigs(nodes, 1e-3)
+    assert np.allclose(lam[1:], closed[1:], rtol=1e-11)
+    gamma, cnt = pins.gap_gamma(lam, 20)
+    assert pins.dense_inertia_count(A, B, gamma) == cnt
+    V1 = si.start_block(p.n, int(np.ceil(1.5 * cnt)), 5)
+    r = orc.enhanced_slrf(A, B, gamma, V1, m=8, it_max=30, outer_max=40)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
+    assert r.resid.max() <= 1e-8
+    assert np.abs(r.X.T @ (B @ r.X) - np.eye(cnt)).max() <= 1e-10
+
+
+def test_solve_elasticity_against_dense_eigh():
+    E = np.exp(np.random.default_rng(9).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    A, B = p.A(), p.B()
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    assert pins.dense_inertia_count(A, B, gamma) == cnt
+    V1 = si.start_block(p.n, int(np.ceil(1.5 * cnt)), 6)
+    r = orc.enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, outer_max=40)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
+    assert r.resid.max() <= 1e-8
+
+
+def test_basic_method_agrees():
+    """Alg. 1 (no locking, zero initial guesses, near-exact inner solves) finds the same
+    eigenvalues.  With zero initial guesses the inner error is relative to ||B v||, so the
+    eigen-residual floor is about tol_in * lambda_max / theta: tol_in = 1e-14 here."""
+    nodes = (5, 5, 4)
+    p, A, B = _small_q1(nodes)
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 12)
+    V1 = si.start_block(p.n, int(np.ceil(1.5 * cnt)), 7)
+    r = orc.enhanced_slrf(A, B, gamma, V1, m=8, it_max=400, tol_in=1e-14, outer_max=30,
+                          lock=False, warm=False)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
+
+
+def test_sturm_count_matches_dense():
+    n = 120
+    p = si.bar1d_pencil(n)
+    h = 1.0 / (n + 1)
+    for gamma in (50.0, 3000.0, 2.0e5):
+        c = pins.sturm_count(np.full(n, 2 / h), np.full(n - 1, -1 / h), gamma,
+                             np.full(n, 4 * h / 6), np.full(n - 1, h / 6))
+        assert c == pins.dense_inertia_count(p.A(), p.B(), gamma) == np.sum(pins.bar1d_eigs(n) < gamma)
