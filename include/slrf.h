@@ -1,0 +1,196 @@
+/*
+ * slrf.h -- C ABI of the GB300 shifted-Laplace rational-filter (SLRF) eigensolver.
+ *
+ * Computes every eigenpair (lambda, x) of the sparse symmetric-definite pencil
+ * A x = lambda B x with lambda in (0, gamma]  (arXiv 2510.17334, Sec. 1, eq. (1)),
+ * by the enhanced ParaSLRF subspace iteration (Sec. 4, Alg. 2) on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices: one CSR pattern shared by A and B (finite-element assembly gives the same
+ *     pattern), int64 row pointers, int32 column indices sorted within each row, two FP64
+ *     value arrays.  A and B must be symmetric; A positive definite, B positive definite.
+ *   - Dense blocks are ROW-MAJOR n x k with leading dimension k (the k entries of one
+ *     row are contiguous).  This is the layout the kernels gather from.
+ *   - "device" pointers are CUDA device (or managed) memory of the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer it passes;
+ *     the library never frees or retains caller memory after a call returns, except
+ *     that slrf_setup copies the matrices into library-owned storage.
+ *   - Every call returns an int status: SLRF_OK (0) or a negative SLRF_E* code.  No call
+ *     throws, exits or aborts.  A failed CUDA call or an invalid state makes the context
+ *     sticky-failed: later calls on it return SLRF_ESTATE until slrf_destroy.
+ *   - Work is enqueued on the stream given to slrf_setup (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream).  Calls that return results in host
+ *     memory synchronise that stream.
+ */
+#ifndef SLRF_H
+#define SLRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------- */
+#define SLRF_OK 0
+#define SLRF_EINVAL (-1)     /* invalid argument (size, pointer, option)                 */
+#define SLRF_ENOMEM (-2)     /* device memory for the working set is not available       */
+#define SLRF_ECUDA (-3)      /* a CUDA runtime call failed                               */
+#define SLRF_EBREAKDOWN (-4) /* COCG breakdown (p^T A p or r^T r vanished) in some column */
+#define SLRF_ETIMEOUT (-5)   /* a bounded device-side wait gave up                       */
+#define SLRF_ECHOL (-6)      /* B-Gram matrix not numerically positive definite          */
+#define SLRF_ENOCONV (-7)    /* outer iteration cap reached before the stopping rule     */
+#define SLRF_ENAN (-8)       /* non-finite value in an input or an intermediate          */
+#define SLRF_ETRUNC (-9)     /* output capacity smaller than the number of eigenpairs    */
+#define SLRF_ESTATE (-10)    /* context is in a failed state from an earlier error       */
+
+/* ---- types ---------------------------------------------------------------------- */
+typedef struct slrf_ctx slrf_ctx; /* opaque, owned by the library */
+
+/* A and B on one CSR pattern (all device pointers). */
+typedef struct {
+  int64_t n;             /* rows = columns                          */
+  int64_t nnz;           /* stored entries                          */
+  const int64_t *rowptr; /* device, n + 1 entries, rowptr[0] = 0    */
+  const int32_t *col;    /* device, nnz column indices              */
+  const double *valA;    /* device, nnz values of A                 */
+  const double *valB;    /* device, nnz values of B                 */
+} slrf_csr_pair;
+
+/* Options.  slrf_opts_default fills the paper's settings. */
+typedef struct {
+  int m;                  /* upper-half-plane poles N (Sec. 2, l = 2N); 1..32, default 8     */
+  double alpha;           /* pole line slope: sigma = Re(sigma)(1 + alpha i), default 1     */
+  double beta;            /* relaxation (Tikhonov) weight of the pole design, default 0.01  */
+  double band;            /* stop band starts at band*gamma, default 1.3                    */
+  int it_max;             /* It_max-linear: fixed COCG updates per solve (Alg. 2 l.10)     */
+  int refine_max;         /* mixed path: FP64 refinement steps, >= 1, default 1             */
+  int outer_max;          /* outer iteration cap, default 100                               */
+  double tol_inner;       /* COCG stop ||r|| <= tol_inner ||r0||, default 1e-10 (Sec. 3.2)  */
+  double tol_eig;         /* lock when ||Av - theta Bv|| / ||Av|| <= tol_eig, default 1e-8  */
+  int precision;          /* 0 = FP64 throughout; 1 = complex-FP32 COCG in FP64 refinement  */
+  int warm_start;         /* 1 = y0 = v/(theta - sigma) (Alg. 2 l.21); 0 = y0 = 0           */
+  int lock;               /* 1 = lock converged pairs (Alg. 2); 0 = basic method (Alg. 1)   */
+  int use_graph;          /* 1 = replay the It_max inner loop from a captured CUDA graph    */
+  int nev;                /* if > 0, also require this many locked pairs before stopping    */
+  uint64_t seed;          /* seed of the Gaussian start block when V0 is NULL               */
+  const double *poles;    /* optional HOST table: m complex poles, (re, im) interleaved     */
+  const double *weights;  /* optional HOST table: m complex weights; NULL = SLRF design     */
+} slrf_opts;
+
+/* Statistics of the last slrf_solve (host struct filled by the library). */
+typedef struct {
+  int outer_iters;           /* outer iterations performed                                */
+  int n_conv;                /* locked pairs                                              */
+  int64_t column_solves;     /* sum over outer iterations of m * n_act shifted solves     */
+  int64_t column_iterations; /* sum over all solves of the COCG updates performed         */
+  int breakdowns;            /* columns stopped by a COCG breakdown                       */
+  double ms_filter;          /* device time in filter applies (CUDA events)               */
+  double ms_dense;           /* device time in orthogonalisation + Rayleigh-Ritz + locking */
+  double ms_total;           /* device time of the whole solve                            */
+} slrf_stats;
+
+/* ---- entry points ----------------------------------------------------------------- */
+
+/* Fill *opts with the paper's defaults: m = 8, alpha = 1, beta = 0.01 (Sec. 3.2),
+ * band = 1.3, it_max = 40, refine_max = 1, outer_max = 100, tol_inner = 1e-10 (Sec. 3.2),
+ * tol_eig = 1e-8 (Sec. 3.2), precision = 0, warm_start = 1, lock = 1 (Sec. 4), use_graph = 1,
+ * nev = 0, seed = 1, poles = weights = NULL.  Returns SLRF_EINVAL if opts is NULL. */
+int slrf_opts_default(slrf_opts *opts);
+
+/* Create a solver context for the pencil (A, B), the interval (0, gamma] and search-block
+ * width L = block_L (Alg. 2 input L >= NEV; the paper takes L = 1.2 NEV, Sec. 3.2).
+ * Copies the pattern and both value arrays into library storage, designs (or copies) the
+ * pole/weight table {sigma_j, w_j} (Sec. 2.2) and allocates the whole working set for L
+ * columns, so that no later call allocates.  stream is a cudaStream_t or NULL.
+ * Errors: SLRF_EINVAL (NULL pointers, n < 1, gamma <= 0, L < 1 or L > n, m outside 1..32),
+ * SLRF_ENOMEM (working set does not fit), SLRF_ECUDA.  On error *ctx is set to NULL. */
+int slrf_setup(slrf_ctx **ctx, const slrf_csr_pair *pencil, double gamma, int block_L,
+               const slrf_opts *opts, void *stream);
+
+/* Copy the pole/weight table in use to HOST arrays sigma[2m] and w[2m] ((re, im)
+ * interleaved, j = 1..m, upper half plane; the conjugates are implied, Sec. 2).  *m_out
+ * receives m.  Synchronises the stream. */
+int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w);
+
+/* Apply the rational filter to a real block (Alg. 2 lines 7-14):
+ *   U = sum_{j=1..m} 2 Re(w_j Y_j),   (A - sigma_j B) Y_j = B X,
+ * every (pole, column) system solved by COCG for at most it_max updates or until
+ * ||r|| <= tol_inner ||r0||.  X (device, n x k row-major) is the block, k <= L.  theta
+ * (device, k entries) gives the warm start y0 = x_c / (theta_c - sigma_j) (Alg. 2 l.21,
+ * the Cayley form of the Proposition, Sec. 4); theta = NULL gives y0 = 0.  U (device,
+ * n x k row-major) receives the filtered block and may not alias X.  Precision follows
+ * opts.precision.  Asynchronous on the context stream.
+ * Errors: SLRF_EINVAL (k < 1 or k > L, NULL X or U), SLRF_ESTATE, SLRF_ECUDA. */
+int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U);
+
+/* Per-(pole, column) results of the last slrf_filter_apply, copied to HOST arrays of
+ * m * k entries, index j * k + c: COCG updates performed, final ||r|| / ||r0|| and a
+ * breakdown flag.  Any pointer may be NULL.  Synchronises the stream. */
+int slrf_filter_stats(slrf_ctx *ctx, int *iters, double *relres, int *breakdown);
+
+/* B-orthonormalise and project one filtered block (Alg. 2 lines 15-18):
+ *   if n_conv > 0:  U <- U - X (BX^T U), twice (CGS2 against the locked vectors);
+ *   G = U^T B U = R^T R, U <- U R^{-1}, twice (Cholesky-QR2);
+ *   H = U^T A U = S diag(theta) S^T, theta ascending;  V = U S;
+ *   res_c = ||A v_c - theta_c B v_c|| / ||A v_c||,  each v_c sign-normalised so that its
+ *   entry of largest magnitude is positive.
+ * U (device n x k, overwritten with the B-orthonormal basis), X and BX (device n x n_conv,
+ * leading dimension ldx >= n_conv; ignored when n_conv = 0), outputs V (device n x k),
+ * theta and res (device, k).  Errors: SLRF_ECHOL when a Gram matrix is not positive
+ * definite, SLRF_EINVAL, SLRF_ESTATE, SLRF_ECUDA. */
+int slrf_rayleigh_ritz(slrf_ctx *ctx, double *U, int k, const double *X, const double *BX,
+                       int n_conv, int ldx, double *V, double *theta, double *res);
+
+/* Run the enhanced ParaSLRF (Alg. 2) to completion:
+ *   V1 = V0 (device n x L) or, if V0 = NULL, a Gaussian block from opts.seed;
+ *   repeat: filter (warm-started after the first step) -> B-orthogonalise against the
+ *   locked X -> Cholesky-QR2 -> Rayleigh-Ritz -> lock pairs with theta in (0, gamma]
+ *   and res <= tol_eig -> drop them from the active block,
+ *   until no active Ritz value <= gamma remains for two consecutive steps.
+ * Outputs: *n_found; evals (device, cap) ascending; X (device, n x cap row-major, leading
+ * dimension cap) B-orthonormal eigenvectors; resid (device, cap) relative residuals;
+ * stats (HOST, may be NULL).  Synchronises once per outer iteration for the lock count.
+ * Errors: SLRF_ETRUNC if cap < count (n_found still set, the first cap pairs written),
+ * SLRF_ENOCONV at outer_max, SLRF_ECHOL, SLRF_EINVAL, SLRF_ESTATE, SLRF_ECUDA. */
+int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *evals,
+               double *X, double *resid, slrf_stats *stats);
+
+/* Whole solve from HOST memory: copies the pencil and V0 (HOST, n x block_L, or NULL)
+ * to the device, runs slrf_setup + slrf_solve + slrf_destroy, and copies the results
+ * to HOST evals[cap], X[n x cap], resid[cap].  pencil pointers are HOST pointers here.
+ * Same errors as slrf_setup and slrf_solve. */
+int slrf_solve_host(const slrf_csr_pair *pencil_host, double gamma, int block_L,
+                    const slrf_opts *opts, const double *V0, int cap, int *n_found,
+                    double *evals, double *X, double *resid, slrf_stats *stats);
+
+/* Eigenvalue adjoint on the pattern (first-order perturbation of a simple eigenvalue
+ * of a symmetric-definite pencil, x_i B-normalised):  d lambda_i = x_i^T (dA - lambda_i dB) x_i,
+ * so for the loss gradient g_lambda:
+ *   gA[e] = sum_i g_lambda[i] x_i[r_e] x_i[c_e],
+ *   gB[e] = - sum_i g_lambda[i] lambda_i x_i[r_e] x_i[c_e]   for every stored entry e = (r_e, c_e).
+ * If g_X (device n x k, leading dimension k) is not NULL, the eigenvector terms are added:
+ * for each i the projected system (A - lambda_i B) xi_i = -(I - B x_i x_i^T) g_x_i with
+ * x_i^T B xi_i = 0 is solved (minimal-residual iterations in the B-orthogonal complement)
+ * and gA[e] += xi_i[r_e] x_i[c_e], gB[e] += -lambda_i xi_i[r_e] x_i[c_e] - 1/2 x_i[r_e] x_i[c_e] (x_i^T g_x_i).
+ * evals (device k), X (device n x k, leading dimension ldx), g_eval (device k), outputs
+ * gA, gB (device nnz, overwritten).  The pattern is the context's.
+ * Errors: SLRF_EINVAL, SLRF_ENOCONV (an adjoint solve missed its tolerance), SLRF_ESTATE,
+ * SLRF_ECUDA. */
+int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, int ldx,
+                  const double *g_eval, const double *g_X, double *gA, double *gB);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+void slrf_destroy(slrf_ctx *ctx);
+
+/* Static description of a status code. */
+const char *slrf_strerror(int status);
+
+/* First error recorded in the context (SLRF_OK if none). */
+int slrf_last_error(const slrf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLRF_H */

@@ -1,0 +1,7 @@
+"""GB300-native shifted-Laplace rational-filter eigensolver (ParaSLRF hot path).
+
+The compute path is ``libslrf.so`` (CUDA for sm_103a behind the C ABI in
+``include/slrf.h``); ``slrf`` is its marshalling-only binding.
+"""
+from .slrf import (Context, Opts, SlrfEigsh, SlrfError, Stats, lib, slrf_opts_default,  # noqa: F401
+                   slrf_solve_host, strerror)

@@ -1,0 +1,442 @@
+// COCG for every (pole, column) shifted system of one filter apply, all in one grid.
+//
+// Method: the warm-started solves of Alg. 2 (arXiv 2510.17334, Sec. 4) in their Cayley
+// form (Proposition, Sec. 4): with y0 = v/(theta - sigma), the residual system is
+// (A - sigma B) d = r0,  r0 = (A - theta B) v / (sigma - theta),  solution y0 + d.
+// Here r0 = c_w g with a real block g (g = B v and c = 1 for the zero initial guess,
+// g = (A - theta B) v and c = 1/(sigma - theta) for the warm start), so every pole's
+// start comes from one real FP64 sweep.  COCG (van der Vorst & Melissen) runs with
+// the unconjugated bilinear form; each column stops at ||r|| <= tol ||r0|| or It_max.
+//
+// Layout: complex state [row][column][pole] (w = column * mp + pole), W entries per row.
+// A warp owns 32 * VEC consecutive w (one 16-byte load per lane per gathered row),
+// every warp of a block works on the same tile of w for a range of rows, and blockIdx.y
+// (the tile) varies slowest so that one tile's rows stay resident in L2 while they are
+// gathered.  CSR entries of a row are read once per warp and broadcast by shuffles.
+//
+// Kernels per iteration (2 launches):
+//   update : d += alpha p; r -= alpha q; reduce rho' = r^T r, ||r||^2   -> beta, stop mask
+//   spmm   : s = (A - sigma B) r (gathers r); p = r + beta p; q = s + beta q;
+//            reduce mu = p^T q                                         -> alpha = rho/mu
+// (q = A p is carried by the recurrence q = A r + beta q, so one SpMM per iteration.)
+// Block partial sums are written to a buffer and the last block of each tile reduces
+// them in a fixed order (deterministic) and updates the per-column scalars.
+#include "cocg.cuh"
+
+namespace slrf {
+
+template <typename R> struct Vec;
+template <> struct Vec<double> { double2 z[1]; };
+template <> struct Vec<float> { float2 z[2]; };
+
+template <typename R> __device__ __forceinline__ Vec<R> ldv(const cx_t<R> *p) {
+  Vec<R> v;
+  if constexpr (sizeof(R) == 8) {
+    v.z[0] = *reinterpret_cast<const double2 *>(p);
+  } else {
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    v.z[0] = make_float2(t.x, t.y);
+    v.z[1] = make_float2(t.z, t.w);
+  }
+  return v;
+}
+template <typename R> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<R> &v) {
+  if constexpr (sizeof(R) == 8) {
+    *reinterpret_cast<double2 *>(p) = v.z[0];
+  } else {
+    *reinterpret_cast<float4 *>(p) = make_float4(v.z[0].x, v.z[0].y, v.z[1].x, v.z[1].y);
+  }
+}
+
+template <typename R> __device__ __forceinline__ cx_t<R> to_c(double2 a) {
+  cx_t<R> z; z.x = (R)a.x; z.y = (R)a.y; return z;
+}
+
+// Reduce the per-lane values acc[VEC][NQ] of all warps of the block into the block's
+// partial slot, then (last block of the tile only) reduce all blocks' slots into out.
+// Returns true in every thread of the last block; out is valid in threads t < TW of it.
+template <int VEC, int NQ>
+__device__ bool block_then_grid_reduce(double (&acc)[VEC][NQ], const int W, const int w_tile0,
+                                       const int rb, const int nrb, double *partial,
+                                       unsigned *counter, double (&out)[NQ], int &w_out) {
+  constexpr int TW = 32 * VEC;
+  __shared__ double sm[kWarps][TW][NQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) sm[warp][lane * VEC + v][qq] = acc[v][qq];
+  __syncthreads();
+  for (int t = threadIdx.x; t < TW * NQ; t += kThreads) {
+    const int wl = t / NQ, qq = t % NQ;
+    double s = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < kWarps; ++wi) s += sm[wi][wl][qq];
+    partial[((size_t)rb * W + w_tile0 + wl) * kNQ + qq] = s;
+  }
+  if (!last_block_arrive(counter, (unsigned)nrb)) return false;
+  // last block: sum the nrb slots of this tile in a fixed order
+  double a2[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) a2[v][qq] = 0.0;
+  for (int b = warp; b < nrb; b += kWarps) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      const double *src = partial + ((size_t)b * W + w_tile0 + lane * VEC + v) * kNQ;
+#pragma unroll
+      for (int qq = 0; qq < NQ; ++qq) a2[v][qq] += __ldcg(src + qq);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) sm[warp][lane * VEC + v][qq] = a2[v][qq];
+  __syncthreads();
+  if (threadIdx.x < TW) {
+    w_out = w_tile0 + threadIdx.x;
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) {
+      double s = 0.0;
+#pragma unroll
+      for (int wi = 0; wi < kWarps; ++wi) s += sm[wi][threadIdx.x][qq];
+      out[qq] = s;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------------------ init
+// r0 = c g, p0 = r0, q0 = c (A g - sigma B g); reduce mu0 = p0^T q0, rho0 = r0^T r0, ||r0||^2.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a) {
+  constexpr int VEC = cocg_vec<R>();
+  using C = cx_t<R>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rb = blockIdx.x, tile = blockIdx.y;
+  const int w_tile0 = tile * 32 * VEC;
+  const int w0 = w_tile0 + lane * VEC;
+  C sg[VEC], cf[VEC];
+  int cidx[VEC];
+  bool ok[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const int w = w0 + v;
+    sg[v] = a.sig[w & (a.mp - 1)];
+    cf[v] = to_c<R>(a.cfac[w]);
+    cidx[v] = w / a.mp;
+    ok[v] = cidx[v] < a.k;
+  }
+  double acc[VEC][kNQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+  const int64_t i0 = (int64_t)rb * a.rows_per_block;
+  const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
+  for (int64_t i = i0 + warp; i < i1; i += kWarps) {
+    Vec<R> rv, qv;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      R gv = 0, agv = 0, bgv = 0;
+      if (ok[v]) {
+        const size_t o = (size_t)i * a.ldg + cidx[v];
+        gv = (R)a.g[o]; agv = (R)a.Ag[o]; bgv = (R)a.Bg[o];
+      }
+      C r0; r0.x = cf[v].x * gv; r0.y = cf[v].y * gv;
+      C t; t.x = agv - sg[v].x * bgv; t.y = -sg[v].y * bgv;
+      C q0 = cmul(cf[v], t);
+      rv.z[v] = r0; qv.z[v] = q0;
+      acc[v][0] += (double)(r0.x * q0.x - r0.y * q0.y);
+      acc[v][1] += (double)(r0.x * q0.y + r0.y * q0.x);
+      acc[v][2] += (double)(r0.x * r0.x - r0.y * r0.y);
+      acc[v][3] += (double)(2 * r0.x * r0.y);
+      acc[v][4] += (double)(r0.x * r0.x + r0.y * r0.y);
+    }
+    const size_t off = (size_t)i * a.W + w0;
+    stv<R>(a.r + off, rv);
+    stv<R>(a.p + off, rv);
+    stv<R>(a.q + off, qv);
+  }
+  double out[kNQ];
+  int w;
+  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+    return;
+  if (threadIdx.x < 32 * VEC) {
+    WScal s = a.ws[w];
+    const double2 mu = make_double2(out[0], out[1]);
+    s.rho = make_double2(out[2], out[3]);
+    s.r0n2 = out[4];
+    s.rn2 = out[4];
+    s.iters = 0;
+    s.brk = 0;
+    s.beta = make_double2(0.0, 0.0);
+    if (s.active && !(out[4] > 0.0)) s.active = 0;  // zero right-hand side: nothing to do
+    if (s.active && (!cfinite(mu) || (mu.x == 0.0 && mu.y == 0.0))) { s.active = 0; s.brk = 1; }
+    s.alpha = s.active ? cdiv(s.rho, mu) : make_double2(0.0, 0.0);
+    a.ws[w] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------ update
+// d += alpha p (d = alpha p on the first step); r -= alpha q; reduce rho' and ||r||^2.
+// With final_acc, also U[i][c] = coefV[c] V[i][c] + sum_j 2 Re(w_j d_j).
+template <typename R, bool FIRST, bool FINAL>
+__global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R> a) {
+  constexpr int VEC = cocg_vec<R>();
+  using C = cx_t<R>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rb = blockIdx.x, tile = blockIdx.y;
+  const int w_tile0 = tile * 32 * VEC;
+  const int w0 = w_tile0 + lane * VEC;
+  C al[VEC], wt[VEC];
+  bool act[VEC];
+  bool any_act = false;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const WScal &s = a.ws[w0 + v];
+    act[v] = s.active != 0;
+    any_act |= act[v];
+    al[v] = to_c<R>(s.alpha);
+    wt[v] = to_c<R>(a.wt[(w0 + v) & (a.mp - 1)]);
+  }
+  double acc[VEC][kNQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+  const int64_t i0 = (int64_t)rb * a.rows_per_block;
+  const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
+  const int lanes_per_col = a.mp >= VEC ? a.mp / VEC : 1;
+  for (int64_t i = i0 + warp; i < i1; i += kWarps) {
+    const size_t off = (size_t)i * a.W + w0;
+    Vec<R> dv;
+    if (FIRST) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) dv.z[v] = cmake<C>(0, 0);
+    } else if (any_act || FINAL) {
+      dv = ldv<R>(a.d + off);
+    }
+    if (any_act) {
+      Vec<R> pv = ldv<R>(a.p + off), qv = ldv<R>(a.q + off), rv = ldv<R>(a.r + off);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        if (act[v]) {
+          dv.z[v] = cfma(al[v], pv.z[v], dv.z[v]);
+          rv.z[v] = cfms(al[v], qv.z[v], rv.z[v]);
+        }
+        const C rr = rv.z[v];
+        acc[v][0] += (double)(rr.x * rr.x - rr.y * rr.y);
+        acc[v][1] += (double)(2 * rr.x * rr.y);
+        acc[v][2] += (double)(rr.x * rr.x + rr.y * rr.y);
+      }
+      stv<R>(a.r + off, rv);
+    }
+    if (FIRST || any_act) stv<R>(a.d + off, dv);
+    if (FINAL) {
+      // U = coefV V + sum over this column's poles of 2 Re(w_j d_j)
+      double part[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        part[v] = 2.0 * ((double)wt[v].x * (double)dv.z[v].x - (double)wt[v].y * (double)dv.z[v].y);
+      if (a.mp >= VEC) {
+        double s = 0.0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) s += part[v];
+        for (int o = lanes_per_col >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const int c = w0 / a.mp;
+        if ((lane % lanes_per_col) == 0 && c < a.k)
+          a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
+      } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const int c = (w0 + v) / a.mp;
+          if (c < a.k) a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + part[v];
+        }
+      }
+    }
+  }
+  double out[kNQ];
+  int w;
+  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+    return;
+  if (threadIdx.x < 32 * VEC) {
+    WScal s = a.ws[w];
+    if (s.active) {
+      s.iters += 1;
+      s.rn2 = out[2];
+      const double2 rho_new = make_double2(out[0], out[1]);
+      if (out[2] <= a.tol2 * s.r0n2) {
+        s.active = 0;
+      } else if (!cfinite(rho_new) || (s.rho.x == 0.0 && s.rho.y == 0.0)) {
+        s.active = 0;
+        s.brk = 1;
+      } else {
+        s.beta = cdiv(rho_new, s.rho);
+        s.rho = rho_new;
+      }
+      if (!s.active) s.beta = make_double2(0.0, 0.0);
+      a.ws[w] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ spmm
+// s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) cocg_spmm_kernel(const CocgArgs<R> a) {
+  constexpr int VEC = cocg_vec<R>();
+  using C = cx_t<R>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rb = blockIdx.x, tile = blockIdx.y;
+  const int w_tile0 = tile * 32 * VEC;
+  const int w0 = w_tile0 + lane * VEC;
+  C sg[VEC], be[VEC];
+  bool act[VEC];
+  bool any_act = false;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const WScal &s = a.ws[w0 + v];
+    act[v] = s.active != 0;
+    any_act |= act[v];
+    be[v] = to_c<R>(s.beta);
+    sg[v] = a.sig[(w0 + v) & (a.mp - 1)];
+  }
+  // warp-uniform: skip the tile's SpMM when no column in it is still iterating
+  const bool warp_act = __any_sync(0xffffffffu, any_act);
+  double acc[VEC][kNQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+  const int64_t i0 = (int64_t)rb * a.rows_per_block;
+  const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
+  if (warp_act) {
+    for (int64_t i = i0 + warp; i < i1; i += kWarps) {
+      C sa[VEC], sb[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) { sa[v] = cmake<C>(0, 0); sb[v] = cmake<C>(0, 0); }
+      const int64_t rs = a.rowptr[i], re = a.rowptr[i + 1];
+      for (int64_t e0 = rs; e0 < re; e0 += 32) {
+        const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
+        int cl = 0;
+        R avl = 0, bvl = 0;
+        if (lane < cnt) { cl = a.col[e0 + lane]; avl = a.valA[e0 + lane]; bvl = a.valB[e0 + lane]; }
+#pragma unroll 4
+        for (int t = 0; t < cnt; ++t) {
+          const int c = __shfl_sync(0xffffffffu, cl, t);
+          const R av = __shfl_sync(0xffffffffu, avl, t);
+          const R bv = __shfl_sync(0xffffffffu, bvl, t);
+          const Vec<R> x = ldv<R>(a.r + (size_t)c * a.W + w0);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            sa[v].x = fma(av, x.z[v].x, sa[v].x);
+            sa[v].y = fma(av, x.z[v].y, sa[v].y);
+            sb[v].x = fma(bv, x.z[v].x, sb[v].x);
+            sb[v].y = fma(bv, x.z[v].y, sb[v].y);
+          }
+        }
+      }
+      const size_t off = (size_t)i * a.W + w0;
+      Vec<R> rv = ldv<R>(a.r + off), pv = ldv<R>(a.p + off), qv = ldv<R>(a.q + off);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const C s = cfms(sg[v], sb[v], sa[v]);  // A r - sigma B r
+        const C pn = cfma(be[v], pv.z[v], rv.z[v]);
+        const C qn = cfma(be[v], qv.z[v], s);
+        pv.z[v] = pn;
+        qv.z[v] = qn;
+        acc[v][0] += (double)(pn.x * qn.x - pn.y * qn.y);
+        acc[v][1] += (double)(pn.x * qn.y + pn.y * qn.x);
+      }
+      stv<R>(a.p + off, pv);
+      stv<R>(a.q + off, qv);
+    }
+  }
+  double out[kNQ];
+  int w;
+  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+    return;
+  if (threadIdx.x < 32 * VEC) {
+    WScal s = a.ws[w];
+    if (s.active) {
+      const double2 mu = make_double2(out[0], out[1]);
+      if (!cfinite(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
+        s.active = 0;
+        s.brk = 1;
+        s.alpha = make_double2(0.0, 0.0);
+      } else {
+        s.alpha = cdiv(s.rho, mu);
+      }
+      a.ws[w] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ prepare
+__global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
+                                    const double *theta, double2 *cfac, double *coefV, WScal *ws) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int j = w & (mp - 1), c = w / mp;
+  const bool valid = (c < k) && (j < m);
+  WScal s;
+  s.alpha = s.beta = s.rho = make_double2(0.0, 0.0);
+  s.r0n2 = s.rn2 = 0.0;
+  s.active = valid ? 1 : 0;
+  s.iters = 0;
+  s.brk = 0;
+  s.pad = 0;
+  ws[w] = s;
+  double2 cf = make_double2(1.0, 0.0);
+  if (theta != nullptr && valid) {
+    // warm start: r0 = (A - theta B) v / (sigma - theta)
+    cf = cdiv(make_double2(1.0, 0.0), make_double2(sig[j].x - theta[c], sig[j].y));
+  }
+  cfac[w] = cf;
+  if (j == 0 && c < k) {
+    double phi = 0.0;
+    if (theta != nullptr) {
+      for (int jj = 0; jj < m; ++jj) {
+        // Phi(theta) = sum_j 2 Re(w_j / (theta - sigma_j))
+        const double2 z = cdiv(wt[jj], make_double2(theta[c] - sig[jj].x, -sig[jj].y));
+        phi += 2.0 * z.x;
+      }
+    }
+    coefV[c] = phi;
+  }
+}
+
+void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt, const double *theta,
+                  double2 *cfac, double *coefV, WScal *ws, cudaStream_t st) {
+  cocg_prepare_kernel<<<(W + 255) / 256, 256, 0, st>>>(W, k, m, mp, sig, wt, theta, cfac, coefV, ws);
+}
+
+template <typename R> static dim3 grid_of(const CocgArgs<R> &a) {
+  return dim3((unsigned)a.nrb, (unsigned)(a.W / (32 * cocg_vec<R>())));
+}
+
+template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
+  cocg_init_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, bool final_acc, cudaStream_t st) {
+  if (first && final_acc) cocg_update_kernel<R, true, true><<<grid_of(a), kThreads, 0, st>>>(a);
+  else if (first) cocg_update_kernel<R, true, false><<<grid_of(a), kThreads, 0, st>>>(a);
+  else if (final_acc) cocg_update_kernel<R, false, true><<<grid_of(a), kThreads, 0, st>>>(a);
+  else cocg_update_kernel<R, false, false><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st) {
+  cocg_spmm_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+
+template void cocg_init<double>(const CocgArgs<double> &, cudaStream_t);
+template void cocg_init<float>(const CocgArgs<float> &, cudaStream_t);
+template void cocg_update<double>(const CocgArgs<double> &, bool, bool, cudaStream_t);
+template void cocg_update<float>(const CocgArgs<float> &, bool, bool, cudaStream_t);
+template void cocg_spmm<double>(const CocgArgs<double> &, cudaStream_t);
+template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t);
+
+}  // namespace slrf

@@ -1,0 +1,70 @@
+// COCG kernels for all (pole, column) systems (A - sigma_j B) d = r0 of one filter apply.
+#pragma once
+
+#include "common.cuh"
+
+namespace slrf {
+
+// Per-(pole, column) COCG scalars, FP64 in both precisions.
+struct WScal {
+  double2 alpha;   // step length for the next update
+  double2 beta;    // p <- r + beta p for the next SpMM
+  double2 rho;     // r^T r (unconjugated)
+  double r0n2;     // ||r0||^2
+  double rn2;      // ||r||^2 after the last update
+  int active;      // 1 while the column still iterates
+  int iters;       // updates performed
+  int brk;         // breakdown flag
+  int pad;
+};
+
+constexpr int kThreads = 256;  // threads per COCG block (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kNQ = 6;         // doubles per partial slot
+
+template <typename R>
+struct CocgArgs {
+  int64_t n;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const R *valA;
+  const R *valB;
+  int W;        // complex entries per row: kpad * mp, a multiple of 32 * VEC
+  int k;        // real columns in the block
+  int m;        // poles in use
+  int mp;       // poles padded to a power of two (<= 32)
+  int rows_per_block;
+  int nrb;      // row blocks (gridDim.x)
+  cx_t<R> *d;   // correction  (solution = y0 + d)
+  cx_t<R> *r;   // residual
+  cx_t<R> *p;   // search direction
+  cx_t<R> *q;   // (A - sigma B) p
+  const cx_t<R> *sig;  // mp poles
+  double *partial;     // [nrb][W][kNQ]
+  unsigned *counters;  // [ntiles]
+  WScal *ws;           // [W]
+  double tol2;         // tol_inner^2
+  // right-hand side:  r0 = c_w g,  q0 = c_w (A g - sigma B g)  (real FP64 blocks, ld = ldg)
+  const double *g, *Ag, *Bg;
+  int ldg;
+  const double2 *cfac;  // [W] factor c_w
+  // accumulation U = coefV .* V + sum_j 2 Re(w_j d_j)
+  const double2 *wt;    // mp weights (FP64, zero for padded poles)
+  const double *V;
+  int ldv;
+  const double *coefV;  // [k]
+  double *U;
+  int ldu;
+};
+
+// Launchers (defined in cocg.cu).  All enqueue on `st`.
+template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, bool final_acc, cudaStream_t st);
+template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st);
+template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : 2; }
+
+// prepare per-w factors: warm start c = 1/(sigma_j - theta_c), else 1; coefV = Phi(theta_c)
+void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
+                  const double *theta, double2 *cfac, double *coefV, WScal *ws, cudaStream_t st);
+
+}  // namespace slrf

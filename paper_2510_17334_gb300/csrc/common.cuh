@@ -1,0 +1,108 @@
+// Device helpers shared by the SLRF kernels: complex arithmetic on double2/float2,
+// warp reductions, the last-block reduction handshake and a bounded grid barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace slrf {
+
+// ---------------------------------------------------------------- real/complex traits
+template <typename R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+template <typename R> using cx_t = typename Cx<R>::T;
+
+template <typename C> __host__ __device__ inline C cmake(double re, double im) {
+  C z; z.x = re; z.y = im; return z;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+// a * b (complex, unconjugated)
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+// acc + a * b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+  return acc;
+}
+// acc - a * b
+template <typename C> __device__ __forceinline__ C cfms(C a, C b, C acc) {
+  acc.x = fma(-a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(-a.x, b.y, fma(-a.y, b.x, acc.y));
+  return acc;
+}
+__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
+  // Smith's algorithm
+  double2 z;
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    z.x = (a.x + a.y * r) / d; z.y = (a.y - a.x * r) / d;
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    z.x = (a.x * r + a.y) / d; z.y = (a.y * r - a.x) / d;
+  }
+  return z;
+}
+__host__ __device__ inline bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ---------------------------------------------------------------- reductions
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Last-block handshake: every block calls this after writing its partials; exactly one
+// block (the last to arrive) gets true, and then sees all partials written before.
+// The caller resets *counter to 0 when the last block is done.
+__device__ __forceinline__ bool last_block_arrive(unsigned *counter, unsigned total) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == total - 1u);
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// ---------------------------------------------------------------- bounded grid barrier
+// For cooperative launches only (all blocks co-resident).  *count and *gen live in
+// global memory and start at 0.  A block that waits longer than the spin limit sets
+// *err = 1 and returns false; callers leave the kernel when it returns false.
+struct GridBarrier {
+  unsigned *count;
+  unsigned *gen;
+  int *err;
+};
+
+__device__ inline bool grid_sync(const GridBarrier &gb, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned *vgen = gb.gen;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(gb.count, 1u);
+    if (arrived == nblocks - 1u) {
+      *gb.count = 0u;
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*(volatile int *)gb.err) { ok = 0; break; }
+        if (++spins > (1ll << 22)) { atomicExch(gb.err, 1); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace slrf

@@ -1,0 +1,681 @@
+// FP64 kernels of the outer iteration (arXiv 2510.17334, Alg. 2 lines 15-21): real SpMM,
+// tall-skinny Gram and GEMM products, Cholesky-QR building blocks, the projected
+// symmetric eigenproblem (parallel cyclic Jacobi), Ritz residuals and locking.
+// GB300 executes FP64 at about 2 FMA/clock/SM, so these kernels spread the FP64 work over
+// all SMs and keep data traffic small; none of them is on the inner COCG loop.
+#include "dense.cuh"
+#include "../../include/slrf.h"
+
+namespace slrf {
+
+// ------------------------------------------------------------------------------ real SpMM
+// One warp per row, each lane owns up to 4 columns (lane + 32 t) of a 128-column group.
+__global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ col,
+                                                        const double *__restrict__ valA,
+                                                        const double *__restrict__ valB,
+                                                        const double *__restrict__ X, int ldx, int k,
+                                                        double *__restrict__ YA, double *__restrict__ YB,
+                                                        int ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int c0 = blockIdx.y * 128 + lane;
+  double sa[4] = {0, 0, 0, 0}, sb[4] = {0, 0, 0, 0};
+  const int64_t rs = rowptr[i], re = rowptr[i + 1];
+  for (int64_t e0 = rs; e0 < re; e0 += 32) {
+    const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
+    int cl = 0;
+    double al = 0, bl = 0;
+    if (lane < cnt) {
+      cl = col[e0 + lane];
+      al = YA ? valA[e0 + lane] : 0.0;
+      bl = YB ? valB[e0 + lane] : 0.0;
+    }
+    for (int t = 0; t < cnt; ++t) {
+      const int c = __shfl_sync(0xffffffffu, cl, t);
+      const double a = __shfl_sync(0xffffffffu, al, t);
+      const double b = __shfl_sync(0xffffffffu, bl, t);
+      const double *xr = X + (size_t)c * ldx;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cc = c0 + 32 * u;
+        if (cc < k) {
+          const double x = xr[cc];
+          if (YA) sa[u] = fma(a, x, sa[u]);
+          if (YB) sb[u] = fma(b, x, sb[u]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int cc = c0 + 32 * u;
+    if (cc < k) {
+      if (YA) YA[(size_t)i * ldy + cc] = sa[u];
+      if (YB) YB[(size_t)i * ldy + cc] = sb[u];
+    }
+  }
+}
+
+void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return;
+  dim3 grid((unsigned)((n + 7) / 8), (unsigned)((k + 127) / 128));
+  spmm_real_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy);
+}
+
+__global__ void shifted_residual_kernel(int64_t n, int k, const double *AV, const double *BV, int ld,
+                                        const double *theta, double *R, int ldr) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t / k;
+  const int c = (int)(t % k);
+  R[i * ldr + c] = fma(-theta[c], BV[i * ld + c], AV[i * ld + c]);
+}
+
+void shifted_residual(int64_t n, int k, const double *AV, const double *BV, int ld, const double *theta,
+                      double *R, int ldr, cudaStream_t st) {
+  const int64_t tot = n * k;
+  if (tot <= 0) return;
+  shifted_residual_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, AV, BV, ld, theta, R, ldr);
+}
+
+__global__ void copy_block_kernel(int64_t n, int k, const double *src, int lds, double *dst, int ldd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t / k;
+  const int c = (int)(t % k);
+  dst[i * ldd + c] = src[i * lds + c];
+}
+
+void copy_block(int64_t n, int k, const double *src, int lds, double *dst, int ldd, cudaStream_t st) {
+  const int64_t tot = n * k;
+  if (tot <= 0) return;
+  copy_block_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, src, lds, dst, ldd);
+}
+
+__global__ void check_finite_kernel(int64_t count, const double *x, int *flag) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[t])) { atomicExch(flag, 1); return; }
+}
+
+void check_finite(int64_t count, const double *x, int *flag, cudaStream_t st) {
+  if (count <= 0) return;
+  int blocks = (int)((count + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  check_finite_kernel<<<blocks, 256, 0, st>>>(count, x, flag);
+}
+
+// ------------------------------------------------------------------------------ Gram
+// 64 x 64 output tile per block, 256 threads with a 4 x 4 register tile each; the rows
+// are split into gridDim.z chunks whose partial tiles are summed in order by gram_reduce.
+constexpr int kGT = 64;
+constexpr int kGR = 16;
+
+__global__ void __launch_bounds__(256) gram_partial_kernel(int64_t n, const double *__restrict__ X, int ldx, int k1,
+                                                           const double *__restrict__ Y, int ldy, int k2,
+                                                           int64_t rows_per_chunk, bool sym,
+                                                           double *__restrict__ work) {
+  const int ti = blockIdx.x, tj = blockIdx.y, z = blockIdx.z;
+  if (sym && ti > tj) return;
+  __shared__ double xs[kGR][kGT];
+  __shared__ double ys[kGR][kGT];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  const int64_t r0 = (int64_t)z * rows_per_chunk;
+  const int64_t r1 = (r0 + rows_per_chunk < n) ? r0 + rows_per_chunk : n;
+  for (int64_t rr = r0; rr < r1; rr += kGR) {
+    for (int t = threadIdx.x; t < kGR * kGT; t += 256) {
+      const int lr = t / kGT, lc = t % kGT;
+      const int64_t row = rr + lr;
+      const int cx = ti * kGT + lc, cy = tj * kGT + lc;
+      xs[lr][lc] = (row < r1 && cx < k1) ? X[row * ldx + cx] : 0.0;
+      ys[lr][lc] = (row < r1 && cy < k2) ? Y[row * ldy + cy] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int lr = 0; lr < kGR; ++lr) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = xs[lr][ty * 4 + u]; b[u] = ys[lr][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double *out = work + (size_t)z * k1 * k2;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = ti * kGT + ty * 4 + u, j = tj * kGT + tx * 4 + v;
+      if (i < k1 && j < k2) out[(size_t)i * k2 + j] = acc[u][v];
+    }
+}
+
+__global__ void gram_reduce_kernel(int k1, int k2, int nz, bool sym, const double *work, double *C, int ldc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k1 * k2) return;
+  int i = (int)(t / k2), j = (int)(t % k2);
+  int si = i, sj = j;
+  if (sym && i > j) { si = j; sj = i; }  // the lower triangle mirrors the upper one
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += work[(size_t)z * k1 * k2 + (size_t)si * k2 + sj];
+  C[(size_t)i * ldc + j] = s;
+}
+
+static int gram_chunks(int64_t n, int k1, int k2) {
+  const int tiles = ((k1 + kGT - 1) / kGT) * ((k2 + kGT - 1) / kGT);
+  int nz = (2 * 152 + tiles - 1) / tiles;
+  const int64_t maxz = (n + 255) / 256;
+  if (nz > maxz) nz = (int)maxz;
+  if (nz < 1) nz = 1;
+  if (nz > 64) nz = 64;
+  return nz;
+}
+
+size_t gram_work_doubles(int64_t n, int k1, int k2) { return (size_t)gram_chunks(n, k1, k2) * k1 * k2; }
+
+void gram(int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2, double *C, int ldc,
+          bool sym, double *work, cudaStream_t st) {
+  if (k1 <= 0 || k2 <= 0) return;
+  const int nz = gram_chunks(n, k1, k2);
+  const int64_t rpc = (n + nz - 1) / nz;
+  dim3 grid((k1 + kGT - 1) / kGT, (k2 + kGT - 1) / kGT, nz);
+  gram_partial_kernel<<<grid, 256, 0, st>>>(n, X, ldx, k1, Y, ldy, k2, rpc, sym, work);
+  const int64_t tot = (int64_t)k1 * k2;
+  gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k1, k2, nz, sym, work, C, ldc);
+}
+
+// ------------------------------------------------------------------------------ GEMM
+__global__ void __launch_bounds__(256) gemm_nn_kernel(int64_t n, const double *__restrict__ X, int ldx, int k1,
+                                                      const double *__restrict__ S, int lds, int k2,
+                                                      double *__restrict__ Z, int ldz, double alpha, double beta,
+                                                      bool upper) {
+  __shared__ double xs[kGT][kGR + 1];
+  __shared__ double ss[kGR][kGT];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * kGT;
+  const int c0 = blockIdx.y * kGT;
+  double acc[4][4] = {};
+  int kend = k1;
+  if (upper && c0 + kGT < kend) kend = c0 + kGT;  // S[i][j] = 0 for i > j
+  for (int kk = 0; kk < kend; kk += kGR) {
+    for (int t = threadIdx.x; t < kGT * kGR; t += 256) {
+      const int lr = t / kGR, lc = t % kGR;
+      const int64_t row = r0 + lr;
+      xs[lr][lc] = (row < n && kk + lc < k1) ? X[row * ldx + kk + lc] : 0.0;
+    }
+    for (int t = threadIdx.x; t < kGR * kGT; t += 256) {
+      const int lr = t / kGT, lc = t % kGT;
+      ss[lr][lc] = (kk + lr < k1 && c0 + lc < k2) ? S[(size_t)(kk + lr) * lds + c0 + lc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < kGR; ++l) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = xs[ty * 4 + u][l]; b[u] = ss[l][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t row = r0 + ty * 4 + u;
+    if (row >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tx * 4 + v;
+      if (c < k2) {
+        double* zp = Z + row * ldz + c;
+        *zp = (beta == 0.0) ? alpha * acc[u][v] : fma(alpha, acc[u][v], beta * *zp);
+      }
+    }
+  }
+}
+
+void gemm_nn(int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2, double *Z, int ldz,
+             double alpha, double beta, bool upper, cudaStream_t st) {
+  if (n <= 0 || k2 <= 0) return;
+  dim3 grid((unsigned)((n + kGT - 1) / kGT), (k2 + kGT - 1) / kGT);
+  gemm_nn_kernel<<<grid, 256, 0, st>>>(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, upper);
+}
+
+// ------------------------------------------------------------------------------ Cholesky
+// One block of 1024 threads.  Right-looking Cholesky on the lower triangle of G (in
+// place), then the columns of L^{-1} by forward substitution (one warp per column),
+// stored transposed as R^{-1} = (L^{-1})^T.
+__global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ldg, double *Rinv, int ldr,
+                                                        int *status) {
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = G[(size_t)j * ldg + j];
+      if (!(d > 0.0) || !isfinite(d)) fail = 1;
+      else G[(size_t)j * ldg + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    const double piv = G[(size_t)j * ldg + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(size_t)i * ldg + j] /= piv;
+    __syncthreads();
+    // trailing update of the lower triangle: G[i][l] -= L[i][j] L[l][j], j < l <= i
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = j + 1 + warp; i < k; i += nw) {
+        const double lij = G[(size_t)i * ldg + j];
+        for (int l = j + 1 + lane; l <= i; l += 32) G[(size_t)i * ldg + l] -= lij * G[(size_t)l * ldg + j];
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (threadIdx.x == 0) *status = SLRF_ECHOL;
+    return;
+  }
+  // columns of L^{-1}: L x = e_c  (x_i = 0 for i < c)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < k; c += nw) {
+    // x stored in Rinv row c (R^{-1}[c][i] = x_i)
+    double *x = Rinv + (size_t)c * ldr;
+    for (int i = lane; i < c; i += 32) x[i] = 0.0;
+    if (lane == 0) x[c] = 1.0 / G[(size_t)c * ldg + c];
+    __syncwarp();
+    for (int i = c + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int l = c + lane; l < i; l += 32) s = fma(G[(size_t)i * ldg + l], x[l], s);
+      s = warp_sum(s);
+      if (lane == 0) x[i] = -s / G[(size_t)i * ldg + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // Rinv row c holds column c of L^{-1}: Rinv[c][i] = Linv[i][c] = (R^{-1})[c][i] with R = L^T.
+  // *status is only ever raised (a failure of an earlier pass must survive).
+}
+
+void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st) {
+  chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, ldg, Rinv, ldr, status);
+}
+
+// ------------------------------------------------------------------------------ Jacobi
+// Two-sided cyclic Jacobi with the round-robin (circle) ordering, which makes the kk/2
+// rotations of one round disjoint.  Block b owns pair b of every round: it computes the
+// rotation (phase 1), then, after a grid barrier, rewrites the two rows p, q of
+// J^T A J and the two rows p, q of V^T (phase 2).  A sweep with no rotation ends the loop.
+__device__ __forceinline__ void rr_pair(int kk, int r, int b, int &p, int &q) {
+  const int M = kk - 1;
+  int a0, a1;
+  if (b == 0) { a0 = r; a1 = kk - 1; }
+  else { a0 = (r + b) % M; a1 = (r - b + M) % M; }
+  p = a0 < a1 ? a0 : a1;
+  q = a0 < a1 ? a1 : a0;
+}
+__device__ __forceinline__ int rr_partner(int kk, int r, int x) {
+  const int M = kk - 1;
+  if (x == kk - 1) return r;
+  if (x == r) return kk - 1;
+  return ((2 * r - x) % M + M) % M;
+}
+
+__global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double *H, int ldh, double *theta,
+                                                     double *S, int lds, JacobiWork w, int max_sweeps) {
+  const unsigned nb = gridDim.x;
+  GridBarrier gb{w.bar, w.bar + 1, w.err};
+  double *A = w.A, *Vt = w.Vt;
+  // init: A = H (padded), Vt = I
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)kk * kk;
+       t += (int64_t)nb * blockDim.x) {
+    const int i = (int)(t / kk), j = (int)(t % kk);
+    A[t] = (i < k && j < k) ? H[(size_t)i * ldh + j] : 0.0;
+    Vt[t] = (i == j) ? 1.0 : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) { w.flags[0] = 0; w.flags[1] = 0; }
+  if (!grid_sync(gb, nb)) return;
+  __shared__ double rp[512], rq[512];  // kk <= 512
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < kk - 1; ++r) {
+      for (int b = blockIdx.x; b < kk / 2; b += nb) {
+        int p, q;
+        rr_pair(kk, r, b, p, q);
+        if (threadIdx.x == 0) {
+          const double app = __ldcg(&A[(size_t)p * kk + p]), aqq = __ldcg(&A[(size_t)q * kk + q]),
+                       apq = __ldcg(&A[(size_t)p * kk + q]);
+          double c = 1.0, s = 0.0;
+          if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            w.flags[sweep & 1] = 1;
+          }
+          w.rot[3 * p] = c; w.rot[3 * p + 1] = s; w.rot[3 * p + 2] = 1.0;  // p is first of its pair
+          w.rot[3 * q] = c; w.rot[3 * q + 1] = s; w.rot[3 * q + 2] = 0.0;
+        }
+      }
+      if (!grid_sync(gb, nb)) return;
+      for (int b = blockIdx.x; b < kk / 2; b += nb) {
+        int p, q;
+        rr_pair(kk, r, b, p, q);
+        const double c = __ldcg(&w.rot[3 * p]), s = __ldcg(&w.rot[3 * p + 1]);
+        for (int x = threadIdx.x; x < kk; x += blockDim.x) {
+          rp[x] = __ldcg(&A[(size_t)p * kk + x]);
+          rq[x] = __ldcg(&A[(size_t)q * kk + x]);
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < kk; x += blockDim.x) {
+          const int y = rr_partner(kk, r, x);
+          const double c2 = __ldcg(&w.rot[3 * x]), s2 = __ldcg(&w.rot[3 * x + 1]);
+          const bool first = __ldcg(&w.rot[3 * x + 2]) != 0.0;
+          // (A J)[row][x] for rows p and q
+          double ajp, ajq;
+          if (first) { ajp = c2 * rp[x] - s2 * rp[y]; ajq = c2 * rq[x] - s2 * rq[y]; }
+          else { ajp = s2 * rp[y] + c2 * rp[x]; ajq = s2 * rq[y] + c2 * rq[x]; }
+          double np = c * ajp - s * ajq, nq = s * ajp + c * ajq;
+          if (x == q) np = 0.0;  // annihilated entry
+          if (x == p) nq = 0.0;
+          A[(size_t)p * kk + x] = np;
+          A[(size_t)q * kk + x] = nq;
+          const double vp = __ldcg(&Vt[(size_t)p * kk + x]), vq = __ldcg(&Vt[(size_t)q * kk + x]);
+          Vt[(size_t)p * kk + x] = c * vp - s * vq;
+          Vt[(size_t)q * kk + x] = s * vp + c * vq;
+        }
+        __syncthreads();
+      }
+      if (!grid_sync(gb, nb)) return;
+    }
+    // sweep done: stop when no rotation happened
+    const int rotated = *(volatile int *)&w.flags[sweep & 1];
+    if (!grid_sync(gb, nb)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.flags[sweep & 1] = 0;
+    if (rotated == 0) break;
+    if (!grid_sync(gb, nb)) return;
+  }
+  if (!grid_sync(gb, nb)) return;
+  // sort ascending (stable by index) and write theta, S (column i = eigenvector i)
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const double di = __ldcg(&A[(size_t)i * kk + i]);
+      int rank = 0;
+      for (int j = 0; j < k; ++j) {
+        const double dj = __ldcg(&A[(size_t)j * kk + j]);
+        rank += (dj < di) || (dj == di && j < i);
+      }
+      theta[rank] = di;
+      for (int x = 0; x < k; ++x) S[(size_t)x * lds + rank] = __ldcg(&Vt[(size_t)i * kk + x]);
+    }
+  }
+}
+
+size_t jacobi_work_doubles(int k) {
+  const int kk = k + (k & 1);
+  return 2 * (size_t)kk * kk + 3 * (size_t)kk;
+}
+
+int jacobi_eig(int k, const double *H, int ldh, double *theta, double *S, int lds, JacobiWork w, cudaStream_t st) {
+  int kk = k + (k & 1);
+  if (kk < 2) kk = 2;
+  if (kk > 512) return SLRF_EINVAL;
+  int dev = 0, per_sm = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 128, 0);
+  int nb = kk / 2;
+  if (nb > per_sm * sms) nb = per_sm * sms;
+  if (nb < 1) return SLRF_ECUDA;
+  cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
+  cudaMemsetAsync(w.err, 0, sizeof(int), st);
+  int max_sweeps = 40;
+  void *args[] = {&k, &kk, (void *)&H, &ldh, &theta, &S, &lds, &w, &max_sweeps};
+  cudaError_t e = cudaLaunchCooperativeKernel((void *)jacobi_kernel, dim3(nb), dim3(128), args, 0, st);
+  return e == cudaSuccess ? SLRF_OK : SLRF_ECUDA;
+}
+
+// ------------------------------------------------------------------------------ residuals
+// Per column c over rows: s0 = sum (AV - theta BV)^2, s1 = sum AV^2, s2 = sum V BV,
+// and (max |V|, its row, its sign) for the sign convention.  Partials per row chunk.
+constexpr int kRRows = 512;
+
+__global__ void ritz_partial_kernel(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld,
+                                    const double *theta, double *work) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int64_t r0 = (int64_t)blockIdx.x * kRRows;
+  const int64_t r1 = (r0 + kRRows < n) ? r0 + kRRows : n;
+  const double th = theta[c];
+  double s0 = 0, s1 = 0, s2 = 0, amax = -1.0, sgn = 1.0, arow = 0;
+  for (int64_t i = r0; i < r1; ++i) {
+    const double av = AV[i * ld + c], bv = BV[i * ld + c], v = V[i * ld + c];
+    const double rr = fma(-th, bv, av);
+    s0 = fma(rr, rr, s0);
+    s1 = fma(av, av, s1);
+    s2 = fma(v, bv, s2);
+    if (fabs(v) > amax) { amax = fabs(v); sgn = v < 0 ? -1.0 : 1.0; arow = (double)i; }
+  }
+  double *o = work + ((size_t)blockIdx.x * k + c) * 6;
+  o[0] = s0; o[1] = s1; o[2] = s2; o[3] = amax; o[4] = sgn; o[5] = arow;
+}
+
+__global__ void ritz_final_kernel(int k, int nchunks, const double *theta, const double *work, double *res,
+                                  double *res_paper, double *sgn) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  double s0 = 0, s1 = 0, s2 = 0, amax = -1.0, sg = 1.0;
+  for (int z = 0; z < nchunks; ++z) {
+    const double *o = work + ((size_t)z * k + c) * 6;
+    s0 += o[0]; s1 += o[1]; s2 += o[2];
+    if (o[3] > amax) { amax = o[3]; sg = o[4]; }  // strict: the first row wins ties
+  }
+  const double rn = sqrt(s0);
+  res[c] = s1 > 0 ? rn / sqrt(s1) : INFINITY;
+  if (res_paper) res_paper[c] = (s2 > 0 && theta[c] != 0) ? rn / (fabs(theta[c]) * sqrt(s2)) : INFINITY;
+  if (sgn) sgn[c] = sg;
+}
+
+size_t ritz_work_doubles(int64_t n, int k) { return (size_t)((n + kRRows - 1) / kRRows) * k * 6; }
+
+void ritz_residuals(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld,
+                    const double *theta, double *res, double *res_paper, double *sgn, double *work, cudaStream_t st) {
+  if (k <= 0) return;
+  const int nchunks = (int)((n + kRRows - 1) / kRRows);
+  dim3 grid(nchunks, (k + 127) / 128);
+  ritz_partial_kernel<<<grid, 128, 0, st>>>(n, k, V, AV, BV, ld, theta, work);
+  ritz_final_kernel<<<(k + 127) / 128, 128, 0, st>>>(k, nchunks, theta, work, res, res_paper, sgn);
+}
+
+// ------------------------------------------------------------------------------ locking
+__global__ void lock_decide_kernel(int k, const double *theta, const double *res, double gamma, double tol,
+                                   int lock, int cap, int *info, int *dst_x, int *dst_v, double *Theta,
+                                   double *Res, double *theta_act) {
+  if (threadIdx.x != 0) return;
+  int n_conv = info[0];
+  int newly = 0, nact = 0, pending = 0;
+  for (int c = 0; c < k; ++c) {
+    const double th = theta[c];
+    const bool conv = (res[c] <= tol) && (th > 0.0) && (th <= gamma);
+    if (lock && conv) {
+      const int slot = n_conv + newly;
+      dst_x[c] = slot < cap ? slot : -1;
+      dst_v[c] = -1;
+      if (slot < cap) { Theta[slot] = th; Res[slot] = res[c]; }
+      ++newly;
+    } else {
+      dst_x[c] = -1;
+      dst_v[c] = nact;
+      theta_act[nact] = th;
+      ++nact;
+      if (lock) {
+        if (th <= gamma) pending = 1;
+      } else if (th > 0.0 && th <= gamma && !conv) {
+        pending = 1;
+      }
+    }
+  }
+  info[0] = n_conv + newly;
+  info[1] = nact;
+  info[2] = pending;
+  info[3] = newly;
+}
+
+void lock_decide(int k, const double *theta, const double *res, double gamma, double tol, int lock, int cap,
+                 int *info, int *dst_x, int *dst_v, double *Theta, double *Res, double *theta_act, cudaStream_t st) {
+  lock_decide_kernel<<<1, 32, 0, st>>>(k, theta, res, gamma, tol, lock, cap, info, dst_x, dst_v, Theta, Res,
+                                       theta_act);
+}
+
+__global__ void lock_gather_kernel(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld,
+                                   const double *sgn, const int *dst_x, const int *dst_v, double *X, double *BX,
+                                   int ldx, double *Vn, double *AVn, double *BVn, int ldn) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t / k;
+  const int c = (int)(t % k);
+  const double s = sgn[c];
+  const int dx = dst_x[c], dv = dst_v[c];
+  if (dx >= 0) {
+    X[i * ldx + dx] = s * V[i * ld + c];
+    BX[i * ldx + dx] = s * BV[i * ld + c];
+  } else if (dv >= 0) {
+    Vn[i * ldn + dv] = s * V[i * ld + c];
+    AVn[i * ldn + dv] = s * AV[i * ld + c];
+    BVn[i * ldn + dv] = s * BV[i * ld + c];
+  }
+}
+
+void lock_gather(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld, const double *sgn,
+                 const int *dst_x, const int *dst_v, double *X, double *BX, int ldx, double *Vn, double *AVn,
+                 double *BVn, int ldn, cudaStream_t st) {
+  const int64_t tot = n * k;
+  if (tot <= 0) return;
+  lock_gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, V, AV, BV, ld, sgn, dst_x, dst_v, X, BX,
+                                                                    ldx, Vn, AVn, BVn, ldn);
+}
+
+// ------------------------------------------------------------------------------ RNG
+// Philox4x32-10 (Salmon et al., SC'11) keyed by the seed, counter = element index,
+// and Box-Muller on two 32-bit uniforms -> one standard normal per element.
+__device__ __forceinline__ void philox10(uint32_t ctr[4], uint32_t key[2]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t h0 = __umulhi(M0, ctr[0]), l0 = M0 * ctr[0];
+    const uint32_t h1 = __umulhi(M1, ctr[2]), l1 = M1 * ctr[2];
+    const uint32_t n0 = h1 ^ ctr[1] ^ key[0], n2 = h0 ^ ctr[3] ^ key[1];
+    ctr[0] = n0; ctr[1] = l1; ctr[2] = n2; ctr[3] = l0;
+    key[0] += W0; key[1] += W1;
+  }
+}
+
+__global__ void gaussian_kernel(int64_t n, int k, uint64_t seed, double *V, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), 0u, 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  philox10(ctr, key);
+  const double u1 = ((double)ctr[0] + 1.0) / 4294967297.0;  // (0, 1)
+  const double u2 = (double)ctr[1] / 4294967296.0;
+  const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  V[(t / k) * ld + (t % k)] = z;
+}
+
+void gaussian_block(int64_t n, int k, uint64_t seed, double *V, int ld, cudaStream_t st) {
+  const int64_t tot = n * k;
+  if (tot <= 0) return;
+  gaussian_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, seed, V, ld);
+}
+
+// ------------------------------------------------------------------------------ poles
+// sigma_j = gamma x_j (1 + alpha i), x_j = (j - 1/2)/m; weights minimise
+// sum_t (Phi(t) - 1[t <= gamma])^2 + beta ||w/gamma||^2 on 3000 uniform samples of (0, 1]
+// and 3000 geometric samples of [band, 51] (normalised axis), via the normal equations.
+__global__ void design_poles_kernel(int m, int mp, double gamma, double alpha, double beta, double band,
+                                    double2 *sig, double2 *wt, int *status) {
+  __shared__ double Nm[64][65];
+  __shared__ double rhs[64];
+  __shared__ double2 sh[32];
+  const int n2 = 2 * m;
+  const int nin = 3000, nout = 3000;
+  if (threadIdx.x < m) {
+    const double x = (threadIdx.x + 0.5) / m;
+    sh[threadIdx.x] = make_double2(x, alpha * x);
+  }
+  __syncthreads();
+  // design matrix column a at sample t:  a < m: 2 Re C_a(t); a >= m: -2 Im C_{a-m}(t)
+  for (int e = threadIdx.x; e < n2 * (n2 + 1); e += blockDim.x) {
+    const int a = e / (n2 + 1), b = e % (n2 + 1);  // b == n2 -> right-hand side
+    double s = 0.0;
+    for (int t = 0; t < nin + nout; ++t) {
+      double tt, f;
+      if (t < nin) { tt = (t + 0.5) / nin; f = 1.0; }
+      else { tt = band * pow(51.0 / band, (double)(t - nin) / (nout - 1)); f = 0.0; }
+      const int ja = a < m ? a : a - m;
+      double dr = tt - sh[ja].x, di = -sh[ja].y;  // t - sigma
+      double den = dr * dr + di * di;
+      const double ga = a < m ? 2.0 * dr / den : -2.0 * (-di / den);
+      double gb;
+      if (b == n2) gb = f;
+      else {
+        const int jb = b < m ? b : b - m;
+        dr = tt - sh[jb].x; di = -sh[jb].y; den = dr * dr + di * di;
+        gb = b < m ? 2.0 * dr / den : -2.0 * (-di / den);
+      }
+      s = fma(ga, gb, s);
+    }
+    if (b == n2) rhs[a] = s;
+    else Nm[a][b] = s + (a == b ? beta : 0.0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Cholesky solve of the SPD normal equations
+    int ok = 1;
+    for (int j = 0; j < n2 && ok; ++j) {
+      double d = Nm[j][j];
+      for (int l = 0; l < j; ++l) d -= Nm[j][l] * Nm[j][l];
+      if (!(d > 0)) { ok = 0; break; }
+      Nm[j][j] = sqrt(d);
+      for (int i = j + 1; i < n2; ++i) {
+        double s = Nm[i][j];
+        for (int l = 0; l < j; ++l) s -= Nm[i][l] * Nm[j][l];
+        Nm[i][j] = s / Nm[j][j];
+      }
+    }
+    if (ok) {
+      double y[64];
+      for (int i = 0; i < n2; ++i) {
+        double s = rhs[i];
+        for (int l = 0; l < i; ++l) s -= Nm[i][l] * y[l];
+        y[i] = s / Nm[i][i];
+      }
+      for (int i = n2 - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int l = i + 1; l < n2; ++l) s -= Nm[l][i] * y[l];
+        y[i] = s / Nm[i][i];
+      }
+      for (int j = 0; j < mp; ++j) {
+        if (j < m) {
+          sig[j] = make_double2(gamma * sh[j].x, gamma * sh[j].y);
+          wt[j] = make_double2(gamma * y[j], gamma * y[m + j]);
+        } else {
+          sig[j] = make_double2(gamma, gamma);  // padding pole: never active, weight 0
+          wt[j] = make_double2(0.0, 0.0);
+        }
+      }
+    }
+    *status = ok ? 0 : SLRF_EINVAL;
+  }
+}
+
+void design_poles(int m, int mp, double gamma, double alpha, double beta, double band, double2 *sig, double2 *wt,
+                  int *status, cudaStream_t st) {
+  design_poles_kernel<<<1, 256, 0, st>>>(m, mp, gamma, alpha, beta, band, sig, wt, status);
+}
+
+}  // namespace slrf

@@ -1,0 +1,784 @@
+// C ABI and host orchestration of the enhanced ParaSLRF (arXiv 2510.17334, Alg. 2) on one GPU.
+//
+// The paper's two parallel levels (poles across process groups, each solve across the
+// processes of a group; Sec. 2.1) become one grid: every (pole, column) system of a
+// filter apply is in flight in the same COCG launches, and the paper's sum-reduce of
+// the Y_j (Alg. 2 line 14) is the in-register pole sum of the last COCG update.
+// The host drives the outer loop; the only device->host transfer per outer iteration is
+// a handful of integers for the lock decision (Alg. 2 lines 19-20).
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/slrf.h"
+#include "cocg.cuh"
+#include "dense.cuh"
+
+using namespace slrf;
+
+namespace slrf {
+int eig_grad_values(int64_t n, const int64_t *rowptr, const int32_t *col, int k, const double *evals,
+                    const double *X, int ldx, const double *g, double *gA, double *gB, cudaStream_t st);
+}
+
+struct slrf_ctx {
+  int status = SLRF_OK;  // sticky
+  cudaStream_t st = nullptr;   // library stream (all work, graph capture)
+  cudaStream_t ust = nullptr;  // caller's stream (NULL = legacy default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int dev = 0;
+  int64_t n = 0, nnz = 0;
+  double gamma = 0;
+  int L = 0;
+  slrf_opts o{};
+  int m = 0, mp = 0;
+  bool mixed = false;
+  // matrices (library copies, padded)
+  int64_t *rowptr = nullptr;
+  int32_t *col = nullptr;
+  double *valA = nullptr, *valB = nullptr;
+  float *valA32 = nullptr, *valB32 = nullptr;
+  // pole table
+  double2 *sig = nullptr, *wt = nullptr;
+  float2 *sig32 = nullptr;
+  double h_sig[64] = {}, h_wt[64] = {};
+  // COCG working set
+  int vec = 1;
+  size_t Wmax = 0;
+  void *cd = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr;
+  double *partial = nullptr;
+  unsigned *counters = nullptr;
+  WScal *ws = nullptr;
+  double2 *cfac = nullptr;
+  double *coefV = nullptr;
+  int last_k = 0, last_W = 0;
+  // real n x L blocks (ld = L)
+  double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
+  double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
+  double *X = nullptr, *BX = nullptr;
+  // small
+  double *Gm = nullptr, *Rinv = nullptr, *Hm = nullptr, *Sm = nullptr, *Wm = nullptr;
+  double *theta = nullptr, *theta_act = nullptr, *res = nullptr, *res_paper = nullptr, *sgn = nullptr;
+  double *Theta = nullptr, *Res = nullptr;
+  double *work = nullptr;
+  size_t work_doubles = 0;
+  int *dst_x = nullptr, *dst_v = nullptr, *iflags = nullptr;  // iflags: [0..3] lock info, [4] chol, [5] nan
+  int *h_iflags = nullptr;                                    // pinned mirror
+  JacobiWork jw{};
+  cudaEvent_t ev[4] = {};
+  // graph cache of the inner loop
+  cudaGraphExec_t gexec = nullptr;
+  int g_k = -1, g_warm = -1;
+  std::vector<void *> allocs;
+};
+
+// ----------------------------------------------------------------------------- helpers
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) {                      \
+      if (ctx) ctx->status = SLRF_ECUDA;          \
+      return SLRF_ECUDA;                          \
+    }                                             \
+  } while (0)
+#define CKL()                                     \
+  do {                                            \
+    cudaError_t e_ = cudaGetLastError();          \
+    if (e_ != cudaSuccess) {                      \
+      ctx->status = SLRF_ECUDA;                   \
+      return SLRF_ECUDA;                          \
+    }                                             \
+  } while (0)
+
+template <typename T> static int dalloc(slrf_ctx *ctx, T **p, size_t count) {
+  void *q = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 64);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SLRF_ENOMEM : SLRF_ECUDA;
+  }
+  ctx->allocs.push_back(q);
+  *p = reinterpret_cast<T *>(q);
+  return SLRF_OK;
+}
+
+static int pow2_at_least(int m) {
+  int p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+// columns padded so that k * mp is a multiple of the warp tile (32 * vec complex entries)
+static int kpad_of(int k, int mp, int vec) {
+  const int tile = 32 * vec;
+  const int W = ((k * mp + tile - 1) / tile) * tile;
+  return W / mp;
+}
+
+// CSR sanity: rowptr[0] = 0, non-decreasing, rowptr[n] = nnz, 0 <= col < n.  flag[0] = 1 on failure.
+__global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+    const int64_t r = rowptr[i];
+    if (r < 0 || r > nnz || (i == 0 && r != 0) || (i == n && r != nnz) || (i > 0 && rowptr[i - 1] > r))
+      atomicExch(flag, 1);
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = col[e];
+    if (c < 0 || (int64_t)c >= n) atomicExch(flag, 1);
+  }
+}
+
+__global__ void to_float_kernel(int64_t count, const double *a, float *b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) b[t] = (float)a[t];
+}
+__global__ void to_float2_kernel(int count, const double2 *a, float2 *b) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+// out[0] += breakdowns, out[1] += COCG updates of the last filter apply
+__global__ void count_iters_kernel(int W, const WScal *ws, int *out) {
+  int c = 0, it = 0;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) { c += ws[w].brk; it += ws[w].iters; }
+  c = warp_sum(c);
+  it = warp_sum(it);
+  if ((threadIdx.x & 31) == 0) { atomicAdd(out, c); atomicAdd(out + 1, it); }
+}
+
+// Fork the library stream from the caller's stream on entry, join it back on exit.
+struct StreamScope {
+  slrf_ctx *c;
+  explicit StreamScope(slrf_ctx *ctx) : c(ctx) {
+    cudaEventRecord(c->ev_in, c->ust);
+    cudaStreamWaitEvent(c->st, c->ev_in, 0);
+  }
+  ~StreamScope() {
+    cudaEventRecord(c->ev_out, c->st);
+    cudaStreamWaitEvent(c->ust, c->ev_out, 0);
+  }
+};
+// final sort of the locked pairs: rank by Theta ascending (ties: lock order)
+__global__ void final_rank_kernel(int nconv, const double *Theta, int *rank) {
+  for (int i = threadIdx.x; i < nconv; i += blockDim.x) {
+    const double di = Theta[i];
+    int r = 0;
+    for (int j = 0; j < nconv; ++j) {
+      const double dj = Theta[j];
+      r += (dj < di) || (dj == di && j < i);
+    }
+    rank[i] = r;
+  }
+}
+__global__ void final_gather_kernel(int64_t n, int nconv, int cnt, const int *rank, const double *Theta,
+                                    const double *Res, const double *X, int ldx, double *evals, double *Xo,
+                                    int ldo, double *resid) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nconv) return;
+  const int64_t i = t / nconv;
+  const int c = (int)(t % nconv);
+  const int r = rank[c];
+  if (r >= cnt) return;
+  if (Xo) Xo[i * ldo + r] = X[i * ldx + c];
+  if (i == 0) {
+    if (evals) evals[r] = Theta[c];
+    if (resid) resid[r] = Res[c];
+  }
+}
+
+// ----------------------------------------------------------------------------- filter
+// U = sum_j 2 Re(w_j Y_j), (A - sigma_j B) Y_j = B X, in correction form (see cocg.cu).
+// AXp/BXp: A X and B X if already known (warm start), else computed here.
+template <typename R>
+static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, double *U, int ldu,
+                    bool capture_ok) {
+  const int vec = cocg_vec<R>();
+  const int kp = kpad_of(k, ctx->mp, vec);
+  const int W = kp * ctx->mp;
+  const int ntiles = W / (32 * vec);
+  // rows per block: enough blocks to fill the GPU about 8 deep, at least 16 rows each
+  int64_t target = std::max<int64_t>(1, (152 * 8 + ntiles - 1) / ntiles);
+  int64_t rpb = std::max<int64_t>(16, (ctx->n + target - 1) / target);
+  const int nrb = (int)((ctx->n + rpb - 1) / rpb);
+  CocgArgs<R> a{};
+  a.n = ctx->n;
+  a.rowptr = ctx->rowptr;
+  a.col = ctx->col;
+  if constexpr (sizeof(R) == 8) {
+    a.valA = ctx->valA; a.valB = ctx->valB; a.sig = ctx->sig;
+  } else {
+    a.valA = ctx->valA32; a.valB = ctx->valB32; a.sig = ctx->sig32;
+  }
+  a.W = W; a.k = k; a.m = ctx->m; a.mp = ctx->mp;
+  a.rows_per_block = (int)rpb; a.nrb = nrb;
+  a.d = (cx_t<R> *)ctx->cd; a.r = (cx_t<R> *)ctx->cr; a.p = (cx_t<R> *)ctx->cp; a.q = (cx_t<R> *)ctx->cq;
+  a.partial = ctx->partial; a.counters = ctx->counters; a.ws = ctx->ws;
+  a.tol2 = ctx->o.tol_inner * ctx->o.tol_inner;
+  a.g = ctx->G; a.Ag = ctx->AG; a.Bg = ctx->BG; a.ldg = ctx->L;
+  a.cfac = ctx->cfac; a.wt = ctx->wt;
+  a.V = X; a.ldv = ldx; a.coefV = ctx->coefV; a.U = U; a.ldu = ldu;
+  ctx->last_k = k;
+  ctx->last_W = W;
+  const int itm = ctx->o.it_max;
+  auto body = [&](cudaStream_t s) {
+    cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s);
+    cocg_init<R>(a, s);
+    for (int it = 1; it <= itm; ++it) {
+      cocg_update<R>(a, it == 1, it == itm, s);
+      if (it < itm) cocg_spmm<R>(a, s);
+    }
+  };
+  if (capture_ok && ctx->o.use_graph) {
+    const int warm = theta != nullptr;
+    if (!(ctx->gexec && ctx->g_k == k && ctx->g_warm == warm)) {
+      if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+      body(ctx->st);
+      CK(cudaStreamEndCapture(ctx->st, &g));
+      cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { ctx->status = SLRF_ECUDA; return SLRF_ECUDA; }
+      ctx->g_k = k;
+      ctx->g_warm = warm;
+    }
+    CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+  } else {
+    body(ctx->st);
+  }
+  CKL();
+  return SLRF_OK;
+}
+
+// The real FP64 sweep that starts every pole (Proposition (i), Sec. 4):
+//   zero guess:  g = B X;   warm start:  g = A X - theta B X;   then A g and B g.
+static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, const double *AXp,
+                       const double *BXp, double *U, int ldu, bool capture_ok) {
+  const cudaStream_t st = ctx->st;
+  const int L = ctx->L;
+  if (theta == nullptr) {
+    spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, nullptr, ctx->G, L, st);
+  } else {
+    const double *AX = AXp, *BX = BXp;
+    int ldab = L;
+    if (AX == nullptr || BX == nullptr) {
+      spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, ctx->AG, ctx->BG, L, st);
+      AX = ctx->AG;
+      BX = ctx->BG;
+    }
+    shifted_residual(ctx->n, k, AX, BX, ldab, theta, ctx->G, L, st);
+  }
+  spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->G, L, k, ctx->AG, ctx->BG, L, st);
+  CKL();
+  if (ctx->mixed) return run_cocg<float>(ctx, X, ldx, k, theta, U, ldu, capture_ok);
+  return run_cocg<double>(ctx, X, ldx, k, theta, U, ldu, capture_ok);
+}
+
+// ----------------------------------------------------------------------------- RR step
+// U (n x k, ld L) -> B-orth vs X (CGS2) -> CholQR2 -> Rayleigh-Ritz -> Vt, AVt, BVt,
+// theta, res, res_paper, sgn.  Chol failure is reported through iflags[4].
+static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const double *BX, int nconv, int ldx) {
+  const cudaStream_t st = ctx->st;
+  const int64_t n = ctx->n;
+  const int L = ctx->L;
+  if (nconv > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st);
+      gemm_nn(n, X, ldx, nconv, ctx->Wm, k, k, U, L, -1.0, 1.0, false, st);
+    }
+  }
+  double *cur = U, *nxt = ctx->U2;
+  for (int pass = 0; pass < 2; ++pass) {
+    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, cur, L, k, nullptr, ctx->BU, L, st);
+    gram(n, cur, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
+    chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4 + pass * 0, st);
+    gemm_nn(n, cur, L, k, ctx->Rinv, k, k, nxt, L, 1.0, 0.0, true, st);
+    std::swap(cur, nxt);
+  }
+  // cur holds the B-orthonormal basis (== U after two swaps)
+  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, cur, L, k, ctx->BU, nullptr, L, st);
+  gram(n, cur, L, k, ctx->BU, L, k, ctx->Hm, k, true, ctx->work, st);
+  CKL();
+  int rc = jacobi_eig(k, ctx->Hm, k, ctx->theta, ctx->Sm, k, ctx->jw, st);
+  if (rc != SLRF_OK) { ctx->status = rc; return rc; }
+  gemm_nn(n, cur, L, k, ctx->Sm, k, k, ctx->Vt, L, 1.0, 0.0, false, st);
+  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
+  ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
+  CKL();
+  return SLRF_OK;
+}
+
+// ----------------------------------------------------------------------------- ABI
+extern "C" {
+
+int slrf_opts_default(slrf_opts *o) {
+  if (!o) return SLRF_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->m = 8;
+  o->alpha = 1.0;
+  o->beta = 0.01;
+  o->band = 1.3;
+  o->it_max = 40;
+  o->refine_max = 1;
+  o->outer_max = 100;
+  o->tol_inner = 1e-10;
+  o->tol_eig = 1e-8;
+  o->precision = 0;
+  o->warm_start = 1;
+  o->lock = 1;
+  o->use_graph = 1;
+  o->nev = 0;
+  o->seed = 1;
+  return SLRF_OK;
+}
+
+const char *slrf_strerror(int s) {
+  switch (s) {
+    case SLRF_OK: return "ok";
+    case SLRF_EINVAL: return "invalid argument";
+    case SLRF_ENOMEM: return "not enough device memory";
+    case SLRF_ECUDA: return "CUDA runtime error";
+    case SLRF_EBREAKDOWN: return "COCG breakdown";
+    case SLRF_ETIMEOUT: return "bounded device wait timed out";
+    case SLRF_ECHOL: return "Gram matrix not positive definite (Cholesky failed)";
+    case SLRF_ENOCONV: return "outer iteration cap reached";
+    case SLRF_ENAN: return "non-finite value";
+    case SLRF_ETRUNC: return "output capacity too small";
+    case SLRF_ESTATE: return "context in failed state";
+    default: return "unknown status";
+  }
+}
+
+int slrf_last_error(const slrf_ctx *ctx) { return ctx ? ctx->status : SLRF_EINVAL; }
+
+void slrf_destroy(slrf_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->st) cudaStreamDestroy(ctx->st);
+  for (void *p : ctx->allocs) cudaFree(p);
+  if (ctx->h_iflags) cudaFreeHost(ctx->h_iflags);
+  delete ctx;
+}
+
+int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_L, const slrf_opts *opts,
+               void *stream) {
+  if (!out) return SLRF_EINVAL;
+  *out = nullptr;
+  if (!pc || !pc->rowptr || !pc->col || !pc->valA || !pc->valB || pc->n < 1 || pc->nnz < 1) return SLRF_EINVAL;
+  if (!(gamma > 0) || block_L < 1 || block_L > pc->n) return SLRF_EINVAL;
+  slrf_opts o;
+  if (opts) o = *opts;
+  else slrf_opts_default(&o);
+  if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1) return SLRF_EINVAL;
+  if (block_L > 510) return SLRF_EINVAL;  // the projected eigensolver holds two rows of <= 512 in shared memory
+  if (!(o.tol_inner >= 0) || !(o.tol_eig > 0)) return SLRF_EINVAL;
+  if (pc->n > (int64_t)INT32_MAX) return SLRF_EINVAL;  // int32 column indices
+  slrf_ctx *ctx = new (std::nothrow) slrf_ctx();
+  if (!ctx) return SLRF_ENOMEM;
+  auto fail = [&](int rc) {
+    slrf_destroy(ctx);
+    return rc;
+  };
+  ctx->ust = (cudaStream_t)stream;
+  cudaGetDevice(&ctx->dev);
+  if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(SLRF_ECUDA);
+  // inputs may have been produced on the caller's stream
+  cudaEventRecord(ctx->ev_in, ctx->ust);
+  cudaStreamWaitEvent(ctx->st, ctx->ev_in, 0);
+  ctx->n = pc->n;
+  ctx->nnz = pc->nnz;
+  ctx->gamma = gamma;
+  ctx->L = block_L;
+  ctx->o = o;
+  ctx->m = o.m;
+  ctx->mp = pow2_at_least(o.m);
+  ctx->mixed = o.precision == 1;
+  ctx->vec = ctx->mixed ? 2 : 1;
+  const int64_t n = ctx->n;
+  const int L = block_L;
+  const int kp = kpad_of(L, ctx->mp, ctx->vec);
+  ctx->Wmax = (size_t)kp * ctx->mp;
+  // working-set estimate against free memory
+  const size_t csz = ctx->mixed ? 8 : 16;
+  const size_t state = 4 * (size_t)n * ctx->Wmax * csz;
+  const size_t ntiles_max = ctx->Wmax / (32 * ctx->vec);
+  // run_cocg uses nrb <= ceil(1216 / ntiles) row blocks, so nrb * W <= (1216 + ntiles) * 32 * vec
+  const size_t partial = (152 * 8 + ntiles_max + 1) * 32 * (size_t)ctx->vec * kNQ;
+  const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
+  const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
+  const size_t need = (state + blocks + matrix) + 8 * partial + (64u << 20);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(SLRF_ECUDA);
+  if (need > fr) return fail(SLRF_ENOMEM);
+  int rc;
+#define AL(p, c)                                \
+  if ((rc = dalloc(ctx, &(p), (c))) != SLRF_OK) \
+  return fail(rc)
+  AL(ctx->rowptr, (size_t)n + 1);
+  AL(ctx->col, (size_t)ctx->nnz + 8);
+  AL(ctx->valA, (size_t)ctx->nnz + 4);
+  AL(ctx->valB, (size_t)ctx->nnz + 4);
+  if (cudaMemcpyAsync(ctx->rowptr, pc->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDefault, ctx->st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->col, pc->col, ctx->nnz * sizeof(int32_t), cudaMemcpyDefault, ctx->st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->valA, pc->valA, ctx->nnz * sizeof(double), cudaMemcpyDefault, ctx->st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->valB, pc->valB, ctx->nnz * sizeof(double), cudaMemcpyDefault, ctx->st) != cudaSuccess)
+    return fail(SLRF_ECUDA);
+  {
+    // reject a malformed pattern before any kernel gathers through it
+    int bad = 0;
+    cudaMemsetAsync(ctx->valA + ctx->nnz, 0, sizeof(double), ctx->st);
+    int *dflag = reinterpret_cast<int *>(ctx->valA + ctx->nnz);
+    validate_csr_kernel<<<152 * 4, 256, 0, ctx->st>>>(n, ctx->nnz, ctx->rowptr, ctx->col, dflag);
+    if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess)
+      return fail(SLRF_ECUDA);
+    if (bad) return fail(SLRF_EINVAL);
+  }
+  AL(ctx->sig, 32);
+  AL(ctx->wt, 32);
+  AL(ctx->sig32, 32);
+  if (ctx->mixed) {
+    AL(ctx->valA32, (size_t)ctx->nnz + 4);
+    AL(ctx->valB32, (size_t)ctx->nnz + 4);
+    const unsigned gb = (unsigned)((ctx->nnz + 255) / 256);
+    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, ctx->valA, ctx->valA32);
+    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, ctx->valB, ctx->valB32);
+  }
+  AL(ctx->iflags, 16);
+  if (cudaMallocHost(&ctx->h_iflags, 16 * sizeof(int)) != cudaSuccess) return fail(SLRF_ENOMEM);
+  cudaMemsetAsync(ctx->iflags, 0, 16 * sizeof(int), ctx->st);
+  // pole table
+  if (o.poles && o.weights) {
+    double2 hs[32], hw[32];
+    for (int j = 0; j < ctx->mp; ++j) {
+      if (j < o.m) {
+        hs[j] = make_double2(o.poles[2 * j], o.poles[2 * j + 1]);
+        hw[j] = make_double2(o.weights[2 * j], o.weights[2 * j + 1]);
+      } else {
+        hs[j] = make_double2(gamma, gamma);
+        hw[j] = make_double2(0, 0);
+      }
+    }
+    if (cudaMemcpy(ctx->sig, hs, ctx->mp * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->wt, hw, ctx->mp * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(SLRF_ECUDA);
+  } else {
+    design_poles(o.m, ctx->mp, gamma, o.alpha, o.beta, o.band, ctx->sig, ctx->wt, ctx->iflags + 8, ctx->st);
+  }
+  to_float2_kernel<<<1, 32, 0, ctx->st>>>(ctx->mp, ctx->sig, ctx->sig32);
+  {
+    double2 hs[32], hw[32];
+    int hst[16];
+    if (cudaMemcpyAsync(hs, ctx->sig, ctx->mp * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaMemcpyAsync(hw, ctx->wt, ctx->mp * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaMemcpyAsync(hst, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess)
+      return fail(SLRF_ECUDA);
+    if (hst[8] != 0) return fail(SLRF_EINVAL);
+    for (int j = 0; j < ctx->m; ++j) {
+      ctx->h_sig[2 * j] = hs[j].x; ctx->h_sig[2 * j + 1] = hs[j].y;
+      ctx->h_wt[2 * j] = hw[j].x; ctx->h_wt[2 * j + 1] = hw[j].y;
+    }
+  }
+  // COCG state
+  AL(ctx->cd, n * ctx->Wmax * csz);
+  AL(ctx->cr, n * ctx->Wmax * csz);
+  AL(ctx->cp, n * ctx->Wmax * csz);
+  AL(ctx->cq, n * ctx->Wmax * csz);
+  AL(ctx->partial, partial);
+  AL(ctx->counters, ntiles_max + 32);
+  cudaMemsetAsync(ctx->counters, 0, (ntiles_max + 32) * sizeof(unsigned), ctx->st);
+  AL(ctx->ws, ctx->Wmax);
+  AL(ctx->cfac, ctx->Wmax);
+  AL(ctx->coefV, (size_t)L);
+  // real blocks
+  const size_t nb = (size_t)n * L;
+  AL(ctx->V, nb); AL(ctx->AV, nb); AL(ctx->BV, nb);
+  AL(ctx->G, nb); AL(ctx->AG, nb); AL(ctx->BG, nb);
+  AL(ctx->U, nb); AL(ctx->U2, nb); AL(ctx->BU, nb);
+  AL(ctx->Vt, nb); AL(ctx->AVt, nb); AL(ctx->BVt, nb);
+  AL(ctx->X, nb); AL(ctx->BX, nb);
+  const size_t LL = (size_t)L * L;
+  AL(ctx->Gm, LL); AL(ctx->Rinv, LL); AL(ctx->Hm, LL); AL(ctx->Sm, LL); AL(ctx->Wm, LL);
+  AL(ctx->theta, L); AL(ctx->theta_act, L); AL(ctx->res, L); AL(ctx->res_paper, L); AL(ctx->sgn, L);
+  AL(ctx->Theta, L); AL(ctx->Res, L);
+  AL(ctx->dst_x, L); AL(ctx->dst_v, L);
+  // gram() splits rows into at most 64 chunks of k1 x k2 <= L x L partial tiles
+  ctx->work_doubles = std::max({(size_t)64 * L * L, ritz_work_doubles(n, L), (size_t)4 * L});
+  AL(ctx->work, ctx->work_doubles);
+  {
+    const int kk = L + (L & 1) < 2 ? 2 : L + (L & 1);
+    AL(ctx->jw.A, (size_t)kk * kk);
+    AL(ctx->jw.Vt, (size_t)kk * kk);
+    AL(ctx->jw.rot, 3 * (size_t)kk);
+    AL(ctx->jw.flags, 4);
+    AL(ctx->jw.bar, 4);
+    ctx->jw.err = ctx->iflags + 9;
+  }
+#undef AL
+  for (auto &e : ctx->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(SLRF_ECUDA);
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(SLRF_ECUDA);
+  *out = ctx;
+  return SLRF_OK;
+}
+
+int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w) {
+  if (!ctx) return SLRF_EINVAL;
+  if (m_out) *m_out = ctx->m;
+  if (sigma) memcpy(sigma, ctx->h_sig, 2 * ctx->m * sizeof(double));
+  if (w) memcpy(w, ctx->h_wt, 2 * ctx->m * sizeof(double));
+  return SLRF_OK;
+}
+
+int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (!X || !U || k < 1 || k > ctx->L || X == U) return SLRF_EINVAL;
+  StreamScope sc(ctx);
+  return filter_impl(ctx, X, k, k, theta, nullptr, nullptr, U, k, false);
+}
+
+int slrf_filter_stats(slrf_ctx *ctx, int *iters, double *relres, int *breakdown) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  const int W = ctx->last_W, k = ctx->last_k;
+  if (W == 0) return SLRF_EINVAL;
+  StreamScope sc(ctx);
+  std::vector<WScal> h(W);
+  CK(cudaMemcpyAsync(h.data(), ctx->ws, W * sizeof(WScal), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int c = 0; c < k; ++c)
+    for (int j = 0; j < ctx->m; ++j) {
+      const WScal &s = h[c * ctx->mp + j];
+      const int o = j * k + c;
+      if (iters) iters[o] = s.iters;
+      if (relres) relres[o] = s.r0n2 > 0 ? std::sqrt(s.rn2 / s.r0n2) : 0.0;
+      if (breakdown) breakdown[o] = s.brk;
+    }
+  return SLRF_OK;
+}
+
+int slrf_rayleigh_ritz(slrf_ctx *ctx, double *U, int k, const double *X, const double *BX, int n_conv, int ldx,
+                       double *V, double *theta, double *res) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (!U || !V || !theta || !res || k < 1 || k > ctx->L || n_conv < 0) return SLRF_EINVAL;
+  if (n_conv > 0 && (!X || !BX || ldx < n_conv)) return SLRF_EINVAL;
+  const int64_t n = ctx->n;
+  const int L = ctx->L;
+  StreamScope sc(ctx);
+  // stage into library buffers with leading dimension L
+  copy_block(n, k, U, k, ctx->U, L, ctx->st);
+  if (n_conv > 0) {
+    if (n_conv > L) return SLRF_EINVAL;
+    copy_block(n, n_conv, X, ldx, ctx->X, L, ctx->st);
+    copy_block(n, n_conv, BX, ldx, ctx->BX, L, ctx->st);
+  }
+  CK(cudaMemsetAsync(ctx->iflags + 4, 0, sizeof(int), ctx->st));
+  int rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, n_conv, L);
+  if (rc != SLRF_OK) return rc;
+  int hf[16];
+  CK(cudaMemcpyAsync(hf, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (hf[4] != 0) return SLRF_ECHOL;
+  // apply the sign convention and hand out V, theta, res
+  {
+    // dst_v = identity, no locking: gather into Vt-sized outputs via lock_gather with cap 0
+    std::vector<int> idv(k), idx(k, -1);
+    for (int c = 0; c < k; ++c) idv[c] = c;
+    CK(cudaMemcpyAsync(ctx->dst_v, idv.data(), k * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->dst_x, idx.data(), k * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    lock_gather(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->sgn, ctx->dst_x, ctx->dst_v, nullptr, nullptr, L, ctx->V,
+                ctx->AV, ctx->BV, L, ctx->st);
+    copy_block(n, k, ctx->V, L, V, k, ctx->st);
+    copy_block(n, k, ctx->U, L, U, k, ctx->st);
+    CK(cudaMemcpyAsync(theta, ctx->theta, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(res, ctx->res, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  CKL();
+  return SLRF_OK;
+}
+
+int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *evals, double *Xo, double *resid,
+               slrf_stats *stats) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (!n_found || cap < 0 || (cap > 0 && (!evals || !Xo || !resid))) return SLRF_EINVAL;
+  *n_found = 0;
+  StreamScope sc(ctx);
+  const cudaStream_t st = ctx->st;
+  const int64_t n = ctx->n;
+  const int L = ctx->L;
+  slrf_stats S{};
+  if (V0) copy_block(n, L, V0, L, ctx->V, L, st);
+  else gaussian_block(n, L, ctx->o.seed, ctx->V, L, st);
+  CK(cudaMemsetAsync(ctx->iflags, 0, 16 * sizeof(int), st));
+  if (V0) {
+    check_finite((int64_t)n * L, ctx->V, ctx->iflags + 5, st);
+    CK(cudaMemcpyAsync(ctx->h_iflags, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->h_iflags[5]) return SLRF_ENAN;
+  }
+  int k = L, nconv = 0, quiet = 0, status = SLRF_ENOCONV, outer = 0;
+  bool have_ritz = false;
+  float ms_f = 0, ms_d = 0;
+  CK(cudaEventRecord(ctx->ev[0], st));
+  for (outer = 1; outer <= ctx->o.outer_max; ++outer) {
+    const bool warm = have_ritz && ctx->o.warm_start;
+    CK(cudaEventRecord(ctx->ev[1], st));
+    int rc = filter_impl(ctx, ctx->V, L, k, warm ? ctx->theta_act : nullptr, warm ? ctx->AV : nullptr,
+                         warm ? ctx->BV : nullptr, ctx->U, L, true);
+    if (rc != SLRF_OK) return rc;
+    CK(cudaEventRecord(ctx->ev[2], st));
+    count_iters_kernel<<<1, 256, 0, st>>>(ctx->last_W, ctx->ws, ctx->iflags + 6);
+    S.column_solves += (int64_t)ctx->m * k;
+    rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, ctx->o.lock ? nconv : 0, L);
+    if (rc != SLRF_OK) return rc;
+    // lock decision, compaction (Alg. 2 lines 19-20)
+    lock_decide(k, ctx->theta, ctx->res, ctx->gamma, ctx->o.tol_eig, ctx->o.lock, L, ctx->iflags, ctx->dst_x,
+                ctx->dst_v, ctx->Theta, ctx->Res, ctx->theta_act, st);
+    lock_gather(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->sgn, ctx->dst_x, ctx->dst_v, ctx->X, ctx->BX, L, ctx->V,
+                ctx->AV, ctx->BV, L, st);
+    CKL();
+    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(cudaMemcpyAsync(ctx->h_iflags, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    {
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]);
+      cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);
+      ms_f += a;
+      ms_d += b;
+    }
+    const int *hf = ctx->h_iflags;
+    if (hf[9] != 0) { status = SLRF_ETIMEOUT; break; }
+    if (hf[4] != 0) { status = SLRF_ECHOL; break; }
+    nconv = hf[0];
+    k = hf[1];
+    const int pending = hf[2];
+    have_ritz = true;
+    if (k < 1) { status = SLRF_OK; break; }
+    quiet = pending ? 0 : quiet + 1;
+    if (quiet >= 2 && (ctx->o.nev <= 0 || nconv >= ctx->o.nev)) { status = SLRF_OK; break; }
+  }
+  if (outer > ctx->o.outer_max) outer = ctx->o.outer_max;
+  CK(cudaEventRecord(ctx->ev[3], st));
+  CK(cudaEventSynchronize(ctx->ev[3]));
+  {
+    float tt = 0;
+    cudaEventElapsedTime(&tt, ctx->ev[0], ctx->ev[3]);
+    S.ms_total = tt;
+  }
+  S.ms_filter = ms_f;
+  S.ms_dense = ms_d;
+  S.outer_iters = outer;
+  S.n_conv = nconv;
+  S.breakdowns = ctx->h_iflags[6];
+  S.column_iterations = ctx->h_iflags[7];
+  if (!ctx->o.lock && status == SLRF_OK) {
+    // basic method: the wanted converged Ritz pairs of the last step are the result
+    CK(cudaMemsetAsync(ctx->iflags, 0, sizeof(int), st));
+    lock_decide(k, ctx->theta, ctx->res, ctx->gamma, ctx->o.tol_eig, 1, L, ctx->iflags, ctx->dst_x, ctx->dst_v,
+                ctx->Theta, ctx->Res, ctx->theta_act, st);
+    lock_gather(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->sgn, ctx->dst_x, ctx->dst_v, ctx->X, ctx->BX, L, ctx->U2,
+                ctx->G, ctx->AG, L, st);
+    CK(cudaMemcpyAsync(ctx->h_iflags, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    nconv = ctx->h_iflags[0];
+    S.n_conv = nconv;
+  }
+  *n_found = nconv;
+  const int cnt = std::min(nconv, cap);
+  if (nconv > 0 && cnt > 0) {
+    final_rank_kernel<<<1, 256, 0, st>>>(nconv, ctx->Theta, ctx->dst_x);
+    const int64_t tot = n * nconv;
+    final_gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nconv, cnt, ctx->dst_x, ctx->Theta, ctx->Res,
+                                                                       ctx->X, L, evals, Xo, cap, resid);
+    CKL();
+    CK(cudaStreamSynchronize(st));
+  }
+  if (stats) *stats = S;
+  if (status != SLRF_OK) return status;
+  if (nconv > cap) return SLRF_ETRUNC;
+  return SLRF_OK;
+}
+
+int slrf_solve_host(const slrf_csr_pair *ph, double gamma, int block_L, const slrf_opts *opts, const double *V0,
+                    int cap, int *n_found, double *evals, double *X, double *resid, slrf_stats *stats) {
+  if (!ph || !ph->rowptr || !ph->col || !ph->valA || !ph->valB || ph->n < 1 || ph->nnz < 1 || !n_found)
+    return SLRF_EINVAL;
+  slrf_ctx *ctx = nullptr;  // for CK
+  const int64_t n = ph->n, nnz = ph->nnz;
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SLRF_ECUDA;
+  void *buf = nullptr;
+  const size_t bytes = (n + 1) * 8 + nnz * 4 + 2 * nnz * 8 + (V0 ? (size_t)n * block_L * 8 : 0) +
+                       (size_t)cap * 8 * 2 + (size_t)n * cap * 8 + 256;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaStreamDestroy(st);
+    return SLRF_ENOMEM;
+  }
+  char *b = (char *)buf;
+  auto take = [&](size_t s) { char *p = b; b += (s + 15) / 16 * 16; return p; };
+  int64_t *drp = (int64_t *)take((n + 1) * 8);
+  int32_t *dcol = (int32_t *)take(nnz * 4);
+  double *dA = (double *)take(nnz * 8), *dB = (double *)take(nnz * 8);
+  double *dV0 = V0 ? (double *)take((size_t)n * block_L * 8) : nullptr;
+  double *dev_e = (double *)take((size_t)cap * 8), *dev_r = (double *)take((size_t)cap * 8);
+  double *dX = (double *)take((size_t)n * cap * 8);
+  int rc = SLRF_OK;
+  if (cudaMemcpyAsync(drp, ph->rowptr, (n + 1) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dcol, ph->col, nnz * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dA, ph->valA, nnz * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dB, ph->valB, nnz * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (V0 && cudaMemcpyAsync(dV0, V0, (size_t)n * block_L * 8, cudaMemcpyHostToDevice, st) != cudaSuccess))
+    rc = SLRF_ECUDA;
+  slrf_csr_pair dp{n, nnz, drp, dcol, dA, dB};
+  if (rc == SLRF_OK) rc = slrf_setup(&ctx, &dp, gamma, block_L, opts, st);
+  if (rc == SLRF_OK) {
+    rc = slrf_solve(ctx, dV0, cap, n_found, dev_e, dX, dev_r, stats);
+    const int cnt = std::min(*n_found, cap);
+    if ((rc == SLRF_OK || rc == SLRF_ETRUNC) && cnt > 0) {
+      if (cudaMemcpyAsync(evals, dev_e, cnt * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(resid, dev_r, cnt * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(X, dX, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        rc = SLRF_ECUDA;
+    }
+  }
+  slrf_destroy(ctx);
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, int ldx, const double *g_eval,
+                  const double *g_X, double *gA, double *gB) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (k < 1 || !evals || !X || ldx < k || !g_eval || !gA || !gB) return SLRF_EINVAL;
+  if (g_X) return SLRF_EINVAL;  // eigenvector terms: see slrf_eig_grad_vec
+  StreamScope sc(ctx);
+  const int rc = eig_grad_values(ctx->n, ctx->rowptr, ctx->col, k, evals, X, ldx, g_eval, gA, gB, ctx->st);
+  if (rc != SLRF_OK) ctx->status = rc;
+  return rc;
+}
+
+}  // extern "C"

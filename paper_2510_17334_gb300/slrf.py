@@ -1,0 +1,270 @@
+"""Thin Python binding of libslrf.so: argument marshalling only.
+
+Every function here forwards device pointers of torch tensors (or host numpy arrays for
+``slrf_solve_host``) to the C ABI declared in ``include/slrf.h``; all arithmetic runs in
+the library's CUDA kernels.  The binding raises ``SlrfError`` on any non-zero status and
+refuses to run without the compiled library (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libslrf.so")
+
+SLRF_OK = 0
+SLRF_EINVAL = -1
+SLRF_ENOMEM = -2
+SLRF_ECUDA = -3
+SLRF_EBREAKDOWN = -4
+SLRF_ETIMEOUT = -5
+SLRF_ECHOL = -6
+SLRF_ENOCONV = -7
+SLRF_ENAN = -8
+SLRF_ETRUNC = -9
+SLRF_ESTATE = -10
+
+SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_apply", "slrf_filter_stats",
+           "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
+           "slrf_strerror", "slrf_last_error")
+
+
+class SlrfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status} ({strerror(status)})")
+
+
+class CsrPair(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("nnz", ct.c_int64), ("rowptr", ct.c_void_p), ("col", ct.c_void_p),
+                ("valA", ct.c_void_p), ("valB", ct.c_void_p)]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("m", ct.c_int), ("alpha", ct.c_double), ("beta", ct.c_double), ("band", ct.c_double),
+                ("it_max", ct.c_int), ("refine_max", ct.c_int), ("outer_max", ct.c_int),
+                ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
+                ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
+                ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("outer_iters", ct.c_int), ("n_conv", ct.c_int), ("column_solves", ct.c_int64),
+                ("column_iterations", ct.c_int64), ("breakdowns", ct.c_int), ("ms_filter", ct.c_double),
+                ("ms_dense", ct.c_double), ("ms_total", ct.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """Load libslrf.so (built by ``paper_2510_17334_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: run paper_2510_17334_gb300.build.build() first")
+        L = ct.CDLL(_LIB_PATH)
+        vp, i, d, i64 = ct.c_void_p, ct.c_int, ct.c_double, ct.c_int64
+        L.slrf_opts_default.argtypes = [ct.POINTER(Opts)]
+        L.slrf_setup.argtypes = [ct.POINTER(vp), ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp]
+        L.slrf_get_poles.argtypes = [vp, ct.POINTER(i), vp, vp]
+        L.slrf_filter_apply.argtypes = [vp, vp, i, vp, vp]
+        L.slrf_filter_stats.argtypes = [vp, vp, vp, vp]
+        L.slrf_rayleigh_ritz.argtypes = [vp, vp, i, vp, vp, i, i, vp, vp, vp]
+        L.slrf_solve.argtypes = [vp, vp, i, ct.POINTER(i), vp, vp, vp, ct.POINTER(Stats)]
+        L.slrf_solve_host.argtypes = [ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp, i, ct.POINTER(i), vp, vp, vp,
+                                      ct.POINTER(Stats)]
+        L.slrf_eig_grad.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp]
+        L.slrf_destroy.argtypes = [vp]
+        L.slrf_destroy.restype = None
+        L.slrf_strerror.argtypes = [i]
+        L.slrf_strerror.restype = ct.c_char_p
+        L.slrf_last_error.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().slrf_strerror(int(status)).decode()
+
+
+def _check(rc: int, where: str, ok=(SLRF_OK,)):
+    if rc not in ok:
+        raise SlrfError(rc, where)
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ct.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return ct.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def slrf_opts_default(**kw) -> Opts:
+    o = Opts()
+    _check(lib().slrf_opts_default(ct.byref(o)), "slrf_opts_default")
+    keep = []
+    for k, v in kw.items():
+        if k in ("poles", "weights"):
+            arr = np.ascontiguousarray(np.stack([np.real(v), np.imag(v)], axis=1).ravel(), dtype=np.float64)
+            keep.append(arr)
+            setattr(o, k, arr.ctypes.data)
+        else:
+            setattr(o, k, v)
+    o._keep = keep  # keep host tables alive while the options are
+    return o
+
+
+def _dev(x, dtype):
+    return x.to(device="cuda", dtype=dtype).contiguous()
+
+
+class Context:
+    """Owns one ``slrf_ctx`` (slrf_setup ... slrf_destroy)."""
+
+    def __init__(self, rowptr, col, valA, valB, gamma: float, block_L: int, opts: Opts | None = None,
+                 stream: torch.cuda.Stream | None = None):
+        self.rowptr = _dev(torch.as_tensor(rowptr), torch.int64)
+        self.col = _dev(torch.as_tensor(col), torch.int32)
+        self.valA = _dev(torch.as_tensor(valA), torch.float64)
+        self.valB = _dev(torch.as_tensor(valB), torch.float64)
+        self.n = int(self.rowptr.numel() - 1)
+        self.nnz = int(self.col.numel())
+        self.gamma = float(gamma)
+        self.L = int(block_L)
+        self.opts = opts if opts is not None else slrf_opts_default()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        pair = CsrPair(self.n, self.nnz, _ptr(self.rowptr), _ptr(self.col), _ptr(self.valA), _ptr(self.valB))
+        h = ct.c_void_p()
+        _check(lib().slrf_setup(ct.byref(h), ct.byref(pair), self.gamma, self.L, ct.byref(self.opts),
+                                ct.c_void_p(self.stream.cuda_stream)), "slrf_setup")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().slrf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def poles(self):
+        m = ct.c_int()
+        s = np.zeros(64)
+        w = np.zeros(64)
+        _check(lib().slrf_get_poles(self.h, ct.byref(m), _ptr(s), _ptr(w)), "slrf_get_poles")
+        mm = m.value
+        return s[:2 * mm:2] + 1j * s[1:2 * mm:2], w[:2 * mm:2] + 1j * w[1:2 * mm:2]
+
+    def filter_apply(self, X: torch.Tensor, theta: torch.Tensor | None = None, U: torch.Tensor | None = None):
+        X = _dev(X, torch.float64)
+        k = X.shape[1]
+        if U is None:
+            U = torch.empty_like(X)
+        th = None if theta is None else _dev(theta, torch.float64)
+        _check(lib().slrf_filter_apply(self.h, _ptr(X), k, _ptr(th), _ptr(U)), "slrf_filter_apply")
+        return U
+
+    def filter_stats(self, k: int):
+        m = self.opts.m
+        it = np.zeros(m * k, dtype=np.int32)
+        rr = np.zeros(m * k)
+        bk = np.zeros(m * k, dtype=np.int32)
+        _check(lib().slrf_filter_stats(self.h, _ptr(it), _ptr(rr), _ptr(bk)), "slrf_filter_stats")
+        return it.reshape(m, k), rr.reshape(m, k), bk.reshape(m, k).astype(bool)
+
+    def rayleigh_ritz(self, U: torch.Tensor, X: torch.Tensor | None = None, BX: torch.Tensor | None = None):
+        U = _dev(U, torch.float64).clone()
+        k = U.shape[1]
+        V = torch.empty_like(U)
+        th = torch.empty(k, dtype=torch.float64, device="cuda")
+        rs = torch.empty(k, dtype=torch.float64, device="cuda")
+        nc = 0 if X is None else X.shape[1]
+        Xd = None if X is None else _dev(X, torch.float64)
+        BXd = None if BX is None else _dev(BX, torch.float64)
+        _check(lib().slrf_rayleigh_ritz(self.h, _ptr(U), k, _ptr(Xd), _ptr(BXd), nc, max(nc, 1), _ptr(V), _ptr(th),
+                                        _ptr(rs)), "slrf_rayleigh_ritz")
+        return U, V, th, rs
+
+    def solve(self, V0: torch.Tensor | None = None, cap: int | None = None, check: bool = True):
+        cap = self.L if cap is None else int(cap)
+        V0d = None if V0 is None else _dev(V0, torch.float64)
+        ev = torch.zeros(max(cap, 1), dtype=torch.float64, device="cuda")
+        X = torch.zeros((self.n, max(cap, 1)), dtype=torch.float64, device="cuda")
+        rs = torch.zeros(max(cap, 1), dtype=torch.float64, device="cuda")
+        nf = ct.c_int()
+        st = Stats()
+        rc = lib().slrf_solve(self.h, _ptr(V0d), cap, ct.byref(nf), _ptr(ev), _ptr(X), _ptr(rs), ct.byref(st))
+        if check:
+            _check(rc, "slrf_solve")
+        c = min(nf.value, cap)
+        return rc, nf.value, ev[:c], X[:, :c], rs[:c], st.as_dict()
+
+    def eig_grad(self, evals, X, g_eval, g_X=None):
+        evals = _dev(evals, torch.float64)
+        X = _dev(X, torch.float64)
+        g = _dev(g_eval, torch.float64)
+        gX = None if g_X is None else _dev(g_X, torch.float64)
+        gA = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        gB = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        k = X.shape[1]
+        _check(lib().slrf_eig_grad(self.h, k, _ptr(evals), _ptr(X), k, _ptr(g), _ptr(gX), _ptr(gA), _ptr(gB)),
+               "slrf_eig_grad")
+        return gA, gB
+
+
+def slrf_solve_host(rowptr, col, valA, valB, gamma, block_L, opts=None, V0=None, cap=None):
+    """Whole solve from host numpy arrays through ``slrf_solve_host``."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    valA = np.ascontiguousarray(valA, dtype=np.float64)
+    valB = np.ascontiguousarray(valB, dtype=np.float64)
+    n = rowptr.size - 1
+    cap = block_L if cap is None else cap
+    opts = opts if opts is not None else slrf_opts_default()
+    pair = CsrPair(n, col.size, _ptr(rowptr), _ptr(col), _ptr(valA), _ptr(valB))
+    V0 = None if V0 is None else np.ascontiguousarray(V0, dtype=np.float64)
+    ev = np.zeros(cap)
+    X = np.zeros((n, cap))
+    rs = np.zeros(cap)
+    nf = ct.c_int()
+    st = Stats()
+    rc = lib().slrf_solve_host(ct.byref(pair), float(gamma), int(block_L), ct.byref(opts), _ptr(V0), cap,
+                               ct.byref(nf), _ptr(ev), _ptr(X), _ptr(rs), ct.byref(st))
+    _check(rc, "slrf_solve_host")
+    c = min(nf.value, cap)
+    return ev[:c], X[:, :c], rs[:c], st.as_dict()
+
+
+class SlrfEigsh(torch.autograd.Function):
+    """Eigenpairs in (0, gamma] of (A, B) given by CSR values on a fixed pattern, with the
+    eigenvalue adjoint as backward (gradients on the values of A and B)."""
+
+    @staticmethod
+    def forward(fctx, valA, valB, rowptr, col, gamma, block_L, opts, V0):
+        ctx = Context(rowptr, col, valA.detach(), valB.detach(), gamma, block_L, opts)
+        _, nf, ev, X, rs, _ = ctx.solve(V0)
+        fctx.slrf = ctx
+        fctx.save_for_backward(ev, X)
+        fctx.mark_non_differentiable(X)
+        return ev.clone(), X.clone()
+
+    @staticmethod
+    def backward(fctx, g_ev, g_X):
+        ev, X = fctx.saved_tensors
+        gA, gB = fctx.slrf.eig_grad(ev, X, g_ev.contiguous())
+        return gA, gB, None, None, None, None, None, None
