@@ -28,14 +28,27 @@ METRIC = "eigenpairs/s and shifted column-solves/s at resid≤1e-8; SpMM HBM GB/
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz
 
 
+# Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
+# over all (pole, column) systems and outer iterations), used to scale the timed oracle
+# sample of the reference arm to a whole solve.
+SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 18, "column_iterations": 326400},
+                "bar1d_2000": {"n_found": 20, "outer": 8, "column_iterations": 358400}}
+
+
 def workload(name: str, it_max: int | None):
     import slrf_inputs as si
 
     if name == "q1_lap_41":
         wl = si.q1_lap(41)
-        wl.it_max = it_max or 60
+        wl.it_max = it_max or 20
         desc = ("3D Q1 Laplacian + consistent mass, 41^3 nodes (n=68,921, 27 nnz/row), Neumann + 1e-3 B, "
                 "gamma=259.0666 (105 eigenpairs), block 160, m=8")
+    elif name.startswith("q1_lap_"):
+        nodes = int(name.split("_")[-1])
+        wl = si.q1_lap(nodes)
+        wl.it_max = it_max or 40
+        desc = (f"3D Q1 Laplacian + consistent mass, {nodes}^3 nodes (n={wl.n}), Neumann + 1e-3 B, "
+                f"gamma={wl.gamma:.4f} ({wl.n_expected} eigenpairs), block {wl.block}, m=8")
     elif name == "bar1d_2000":
         wl = si.bar1d(2000)
         wl.it_max = it_max or 200
@@ -142,6 +155,8 @@ def main():
     ap.add_argument("--it-max", type=int, default=None)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-it-max", type=int, default=30,
+                    help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -216,6 +231,33 @@ def main():
         e2e_s = time.perf_counter() - t0
         h2d = hrp.nbytes + hcol.nbytes + hA.nbytes + hB.nbytes + hV0.nbytes
         d2h = ev_h.nbytes * 2 + p.n * wl.block * 8
+        mixed = None
+        if args.precision == 0 and args.mixed_it_max > 0:
+            # the same workload with complex-FP32 inner solves inside the FP64 outer loop
+            mopts = slrf.slrf_opts_default(m=wl.m, it_max=args.mixed_it_max, precision=1)
+            mctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, mopts, stream=stream)
+            for _ in range(args.warmup):
+                mctx.solve(V0)
+            barrier()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            mfound = []
+            m0.record(stream)
+            for _ in range(args.steps):
+                mres = mctx.solve(V0)
+                mfound.append(mres[1])
+            m1.record(stream)
+            barrier()
+            mms = m0.elapsed_time(m1)
+            mev = mres[2].cpu().numpy()
+            fev = ev.cpu().numpy()
+            dev_ = float(np.max(np.abs(mev - fev) / fev)) if len(mev) == len(fev) else None
+            mixed = {"value": sum(mfound) * world / (mms / 1e3), "unit": "eigenpairs/s", "it_max": args.mixed_it_max,
+                     "ms_per_step": mms / args.steps, "eigenpairs_found": mres[1],
+                     "max_resid": float(mres[4].max().item()),
+                     "max_rel_eig_diff_vs_fp64": dev_, "outer_iters": mres[5]["outer_iters"],
+                     "ms_filter_per_step": mres[5]["ms_filter"], "ms_dense_per_step": mres[5]["ms_dense"]}
+            mctx.close()
 
     total_pairs = sum(found) * world
     value = total_pairs / (ms_max / 1e3)
@@ -260,6 +302,7 @@ def main():
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "mixed_precision": mixed,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args.workload, wl.it_max, nf, int(col_iters / args.steps),
@@ -284,27 +327,21 @@ def cpu_baseline_subprocess(name, it_max, n_found, col_iters, outer):
 
 
 def reference_arm(args, rank, world):
-    """The oracle as it stands on the host cores, same workload, metric and unit; each step
-    is a bounded sample (see cpu_baseline_sample), scaled with the GPU solve's iteration
-    counts recorded for this workload."""
+    """The oracle as it stands on the host cores, same workload, metric and unit.  Each step
+    is a bounded sample (cpu_baseline_sample) scaled to one whole solve with the workload's
+    recorded solve counts.  Under torchrun only rank 0 works."""
     if rank != 0:
         return
     wl, desc = workload(args.workload, args.it_max)
-    counts = {"q1_lap_41": (105, None, None), "bar1d_2000": (20, None, None)}
-    n_found = counts.get(args.workload, (0,))[0]
-    # iteration counts of the GPU solve for this workload (column-iterations, outer)
-    ref_counts = {"q1_lap_41": (None, None), "bar1d_2000": (None, None)}
-    ci, outer = ref_counts.get(args.workload, (None, None))
-    if ci is None:
-        # a full oracle solve is hours long at this size: assume every column runs It_max
-        # updates for 16 outer iterations with the block shrinking linearly to L - count
-        L = wl.block
-        outer = 16
-        ci = int(sum(wl.m * (L - (L - (L - n_found)) * 0) * wl.it_max for _ in range(outer)))
+    cnt = SOLVE_COUNTS.get(args.workload)
+    if cnt is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no recorded solve counts for {args.workload}"}))
+        return
     vals = []
     t_start = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline_sample(args.workload, wl.it_max, n_found, ci, outer, budget_s=8.0)
+        r = cpu_baseline_sample(args.workload, wl.it_max, cnt["n_found"], cnt["column_iterations"], cnt["outer"],
+                                budget_s=8.0)
         if s >= args.warmup:
             vals.append(r)
     v = statistics.median([r["value"] for r in vals])

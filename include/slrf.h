@@ -88,6 +88,7 @@ typedef struct {
   double ms_filter;          /* device time in filter applies (CUDA events)               */
   double ms_dense;           /* device time in orthogonalisation + Rayleigh-Ritz + locking */
   double ms_total;           /* device time of the whole solve                            */
+  int64_t kernel_launches;   /* kernels the solve enqueued (graph nodes included)          */
 } slrf_stats;
 
 /* ---- entry points ----------------------------------------------------------------- */
@@ -123,6 +124,15 @@ int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w);
  * opts.precision.  Asynchronous on the context stream.
  * Errors: SLRF_EINVAL (k < 1 or k > L, NULL X or U), SLRF_ESTATE, SLRF_ECUDA. */
 int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U);
+
+/* Measurement hook: the same computation and result as slrf_filter_apply, launched
+ * kernel by kernel (no CUDA graph) with CUDA events around every COCG launch on the
+ * library stream.  HOST outputs: ms[0] total device time of the call, ms[1] summed time
+ * of the fused shifted-SpMM + COCG phase-1 launches, ms[2] summed time of the update
+ * launches, ms[3] the initialisation launch; launches[0] / launches[1] (may be NULL) the
+ * number of SpMM / update launches.  Synchronises the stream. */
+int slrf_filter_timing(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U, double *ms,
+                       int *launches);
 
 /* Per-(pole, column) results of the last slrf_filter_apply, copied to HOST arrays of
  * m * k entries, index j * k + c: COCG updates performed, final ||r|| / ||r0|| and a

@@ -307,3 +307,19 @@ def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, o
         X = Xout
     order = np.argsort(Theta, kind="stable")
     return SolveResult(status, Theta[order], X[:, order], Res[order], k, trace)
+
+
+# ----------------------------------------------------------------------------------------
+# a12: eigenvalue adjoint on the pattern
+# ----------------------------------------------------------------------------------------
+def eig_grad_values(rowptr, col, evals, X, g_eval):
+    """dL/dA_e and dL/dB_e for L with dL/dlambda_i = g_i, every stored entry e = (r, c) an
+    independent parameter:  d lambda_i = x_i^T (dA - lambda_i dB) x_i  for B-normalised x_i
+    (first-order perturbation of a simple eigenvalue of a symmetric-definite pencil)."""
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    # per entry: sum_i g_i x_i[r] x_i[c] and sum_i g_i lambda_i x_i[r] x_i[c]
+    prod = X[rows, :] * X[np.asarray(col), :]
+    gA = prod @ np.asarray(g_eval)
+    gB = -(prod @ (np.asarray(g_eval) * np.asarray(evals)))
+    return gA, gB

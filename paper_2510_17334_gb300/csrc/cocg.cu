@@ -126,9 +126,15 @@ __global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a
   for (int v = 0; v < VEC; ++v) {
     const int w = w0 + v;
     sg[v] = a.sig[w & (a.mp - 1)];
-    cf[v] = to_c<R>(a.cfac[w]);
     cidx[v] = w / a.mp;
     ok[v] = cidx[v] < a.k;
+    double2 c = a.cfac[w];
+    if (a.gscale != nullptr && ok[v]) {
+      const double gs = a.gscale[cidx[v]];
+      c.x *= gs;
+      c.y *= gs;
+    }
+    cf[v] = to_c<R>(c);
   }
   double acc[VEC][kNQ];
 #pragma unroll
@@ -248,13 +254,17 @@ __global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R>
         for (int v = 0; v < VEC; ++v) s += part[v];
         for (int o = lanes_per_col >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const int c = w0 / a.mp;
-        if ((lane % lanes_per_col) == 0 && c < a.k)
+        if ((lane % lanes_per_col) == 0 && c < a.k) {
+          if (a.gscale != nullptr) s /= a.gscale[c];
           a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
+        }
       } else {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const int c = (w0 + v) / a.mp;
-          if (c < a.k) a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + part[v];
+          if (c < a.k)
+            a.U[(size_t)i * a.ldu + c] =
+                a.coefV[c] * a.V[(size_t)i * a.ldv + c] + (a.gscale ? part[v] / a.gscale[c] : part[v]);
         }
       }
     }
@@ -408,6 +418,28 @@ __global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *
     }
     coefV[c] = phi;
   }
+}
+
+// gscale[c] = 1 / max_i |g[i][c]| (1 for a zero column).  Positive doubles order like
+// their bit patterns, so the column maximum is an integer atomicMax.
+__global__ void col_absmax_kernel(int64_t n, int k, const double *g, int ld, unsigned long long *mx) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  double m = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) m = fmax(m, fabs(g[i * ld + c]));
+  atomicMax(mx + c, (unsigned long long)__double_as_longlong(m));
+}
+__global__ void col_scale_kernel(int k, const unsigned long long *mx, double *gscale) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const double m = __longlong_as_double((long long)mx[c]);
+  gscale[c] = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
+}
+void col_scale(int64_t n, int k, const double *g, int ld, unsigned long long *tmp, double *gscale, cudaStream_t st) {
+  cudaMemsetAsync(tmp, 0, k * sizeof(unsigned long long), st);
+  dim3 grid((unsigned)(n < 512 ? n : 512), (k + 127) / 128);
+  col_absmax_kernel<<<grid, 128, 0, st>>>(n, k, g, ld, tmp);
+  col_scale_kernel<<<(k + 127) / 128, 128, 0, st>>>(k, tmp, gscale);
 }
 
 void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt, const double *theta,

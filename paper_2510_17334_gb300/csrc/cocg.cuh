@@ -48,6 +48,8 @@ struct CocgArgs {
   const double *g, *Ag, *Bg;
   int ldg;
   const double2 *cfac;  // [W] factor c_w
+  const double *gscale; // [k] or null: the FP32 path solves for g * gscale (no underflow),
+                        // and the pole sum is divided by gscale again
   // accumulation U = coefV .* V + sum_j 2 Re(w_j d_j)
   const double2 *wt;    // mp weights (FP64, zero for padded poles)
   const double *V;
@@ -62,6 +64,9 @@ template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);
 template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, bool final_acc, cudaStream_t st);
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st);
 template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : 2; }
+
+// gscale[c] = 1 / max |g[:, c]| (tmp: k words of scratch)
+void col_scale(int64_t n, int k, const double *g, int ld, unsigned long long *tmp, double *gscale, cudaStream_t st);
 
 // prepare per-w factors: warm start c = 1/(sigma_j - theta_c), else 1; coefV = Phi(theta_c)
 void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,

@@ -56,7 +56,10 @@ struct slrf_ctx {
   WScal *ws = nullptr;
   double2 *cfac = nullptr;
   double *coefV = nullptr;
+  double *gscale = nullptr;          // FP32 path: per-column right-hand-side scale
+  unsigned long long *gmax = nullptr;
   int last_k = 0, last_W = 0;
+  int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
   // real n x L blocks (ld = L)
   double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
   double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
@@ -195,9 +198,15 @@ __global__ void final_gather_kernel(int64_t n, int nconv, int cnt, const int *ra
 // ----------------------------------------------------------------------------- filter
 // U = sum_j 2 Re(w_j Y_j), (A - sigma_j B) Y_j = B X, in correction form (see cocg.cu).
 // AXp/BXp: A X and B X if already known (warm start), else computed here.
+// Optional per-kernel timing of one filter apply (measurement hook, direct launches).
+struct FilterTiming {
+  double ms_init = 0, ms_spmm = 0, ms_update = 0;
+  int n_spmm = 0, n_update = 0;
+};
+
 template <typename R>
 static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, double *U, int ldu,
-                    bool capture_ok) {
+                    bool capture_ok, FilterTiming *tm) {
   const int vec = cocg_vec<R>();
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
@@ -222,19 +231,63 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   a.tol2 = ctx->o.tol_inner * ctx->o.tol_inner;
   a.g = ctx->G; a.Ag = ctx->AG; a.Bg = ctx->BG; a.ldg = ctx->L;
   a.cfac = ctx->cfac; a.wt = ctx->wt;
+  a.gscale = sizeof(R) == 4 ? ctx->gscale : nullptr;
   a.V = X; a.ldv = ldx; a.coefV = ctx->coefV; a.U = U; a.ldu = ldu;
   ctx->last_k = k;
   ctx->last_W = W;
   const int itm = ctx->o.it_max;
+  ctx->launches += 2 * itm + 1 + (sizeof(R) == 4 ? 3 : 0);
   auto body = [&](cudaStream_t s) {
     cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s);
+    if (sizeof(R) == 4) col_scale(ctx->n, k, ctx->G, ctx->L, ctx->gmax, ctx->gscale, s);
     cocg_init<R>(a, s);
     for (int it = 1; it <= itm; ++it) {
       cocg_update<R>(a, it == 1, it == itm, s);
       if (it < itm) cocg_spmm<R>(a, s);
     }
   };
-  if (capture_ok && ctx->o.use_graph) {
+  if (tm != nullptr) {
+    // same launches, each bracketed by events on the library stream
+    std::vector<cudaEvent_t> ev(2 * (2 * itm + 1));
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    cudaStream_t s = ctx->st;
+    int e = 0;
+    cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s);
+    if (sizeof(R) == 4) col_scale(ctx->n, k, ctx->G, ctx->L, ctx->gmax, ctx->gscale, s);
+    cudaEventRecord(ev[e++], s);
+    cocg_init<R>(a, s);
+    cudaEventRecord(ev[e++], s);
+    for (int it = 1; it <= itm; ++it) {
+      cudaEventRecord(ev[e++], s);
+      cocg_update<R>(a, it == 1, it == itm, s);
+      cudaEventRecord(ev[e++], s);
+      if (it < itm) {
+        cudaEventRecord(ev[e++], s);
+        cocg_spmm<R>(a, s);
+        cudaEventRecord(ev[e++], s);
+      }
+    }
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    float t = 0;
+    e = 0;
+    cudaEventElapsedTime(&t, ev[0], ev[1]);
+    tm->ms_init += t;
+    e = 2;
+    for (int it = 1; it <= itm; ++it) {
+      cudaEventElapsedTime(&t, ev[e], ev[e + 1]);
+      tm->ms_update += t;
+      tm->n_update++;
+      e += 2;
+      if (it < itm) {
+        cudaEventElapsedTime(&t, ev[e], ev[e + 1]);
+        tm->ms_spmm += t;
+        tm->n_spmm++;
+        e += 2;
+      }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+  } else if (capture_ok && ctx->o.use_graph) {
     const int warm = theta != nullptr;
     if (!(ctx->gexec && ctx->g_k == k && ctx->g_warm == warm)) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
@@ -259,11 +312,12 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
 // The real FP64 sweep that starts every pole (Proposition (i), Sec. 4):
 //   zero guess:  g = B X;   warm start:  g = A X - theta B X;   then A g and B g.
 static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, const double *AXp,
-                       const double *BXp, double *U, int ldu, bool capture_ok) {
+                       const double *BXp, double *U, int ldu, bool capture_ok, FilterTiming *tm = nullptr) {
   const cudaStream_t st = ctx->st;
   const int L = ctx->L;
   if (theta == nullptr) {
     spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, nullptr, ctx->G, L, st);
+    ctx->launches += 1;
   } else {
     const double *AX = AXp, *BX = BXp;
     int ldab = L;
@@ -271,13 +325,16 @@ static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
       spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, ctx->AG, ctx->BG, L, st);
       AX = ctx->AG;
       BX = ctx->BG;
+      ctx->launches += 1;
     }
     shifted_residual(ctx->n, k, AX, BX, ldab, theta, ctx->G, L, st);
+    ctx->launches += 1;
   }
   spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->G, L, k, ctx->AG, ctx->BG, L, st);
+  ctx->launches += 1;
   CKL();
-  if (ctx->mixed) return run_cocg<float>(ctx, X, ldx, k, theta, U, ldu, capture_ok);
-  return run_cocg<double>(ctx, X, ldx, k, theta, U, ldu, capture_ok);
+  if (ctx->mixed) return run_cocg<float>(ctx, X, ldx, k, theta, U, ldu, capture_ok, tm);
+  return run_cocg<double>(ctx, X, ldx, k, theta, U, ldu, capture_ok, tm);
 }
 
 // ----------------------------------------------------------------------------- RR step
@@ -287,6 +344,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   const cudaStream_t st = ctx->st;
   const int64_t n = ctx->n;
   const int L = ctx->L;
+  ctx->launches += (nconv > 0 ? 6 : 0) + 10 + 8;
   if (nconv > 0) {
     for (int pass = 0; pass < 2; ++pass) {
       gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st);
@@ -505,6 +563,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   AL(ctx->ws, ctx->Wmax);
   AL(ctx->cfac, ctx->Wmax);
   AL(ctx->coefV, (size_t)L);
+  AL(ctx->gscale, (size_t)L);
+  AL(ctx->gmax, (size_t)L);
   // real blocks
   const size_t nb = (size_t)n * L;
   AL(ctx->V, nb); AL(ctx->AV, nb); AL(ctx->BV, nb);
@@ -551,6 +611,36 @@ int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta
   if (!X || !U || k < 1 || k > ctx->L || X == U) return SLRF_EINVAL;
   StreamScope sc(ctx);
   return filter_impl(ctx, X, k, k, theta, nullptr, nullptr, U, k, false);
+}
+
+int slrf_filter_timing(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U, double *ms,
+                       int *launches) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (!X || !U || !ms || k < 1 || k > ctx->L || X == U) return SLRF_EINVAL;
+  StreamScope sc(ctx);
+  FilterTiming tm;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaEventRecord(e0, ctx->st);
+  const int rc = filter_impl(ctx, X, k, k, theta, nullptr, nullptr, U, k, false, &tm);
+  cudaEventRecord(e1, ctx->st);
+  CK(cudaEventSynchronize(e1));
+  float tot = 0;
+  cudaEventElapsedTime(&tot, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SLRF_OK) return rc;
+  ms[0] = tot;
+  ms[1] = tm.ms_spmm;
+  ms[2] = tm.ms_update;
+  ms[3] = tm.ms_init;
+  if (launches) {
+    launches[0] = tm.n_spmm;
+    launches[1] = tm.n_update;
+  }
+  return SLRF_OK;
 }
 
 int slrf_filter_stats(slrf_ctx *ctx, int *iters, double *relres, int *breakdown) {
@@ -636,6 +726,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
     if (ctx->h_iflags[5]) return SLRF_ENAN;
   }
   int k = L, nconv = 0, quiet = 0, status = SLRF_ENOCONV, outer = 0;
+  ctx->launches = V0 ? 2 : 1;
   bool have_ritz = false;
   float ms_f = 0, ms_d = 0;
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -647,6 +738,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
     if (rc != SLRF_OK) return rc;
     CK(cudaEventRecord(ctx->ev[2], st));
     count_iters_kernel<<<1, 256, 0, st>>>(ctx->last_W, ctx->ws, ctx->iflags + 6);
+    ctx->launches += 1 + 2;  // + lock_decide, lock_gather below
     S.column_solves += (int64_t)ctx->m * k;
     rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, ctx->o.lock ? nconv : 0, L);
     if (rc != SLRF_OK) return rc;
@@ -691,6 +783,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
   S.n_conv = nconv;
   S.breakdowns = ctx->h_iflags[6];
   S.column_iterations = ctx->h_iflags[7];
+  S.kernel_launches = ctx->launches + (nconv > 0 ? 2 : 0);
   if (!ctx->o.lock && status == SLRF_OK) {
     // basic method: the wanted converged Ritz pairs of the last step are the result
     CK(cudaMemsetAsync(ctx->iflags, 0, sizeof(int), st));

@@ -28,7 +28,8 @@ SLRF_ENAN = -8
 SLRF_ETRUNC = -9
 SLRF_ESTATE = -10
 
-SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_apply", "slrf_filter_stats",
+SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_apply", "slrf_filter_timing",
+           "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
            "slrf_strerror", "slrf_last_error")
 
@@ -55,7 +56,7 @@ class Opts(ct.Structure):
 class Stats(ct.Structure):
     _fields_ = [("outer_iters", ct.c_int), ("n_conv", ct.c_int), ("column_solves", ct.c_int64),
                 ("column_iterations", ct.c_int64), ("breakdowns", ct.c_int), ("ms_filter", ct.c_double),
-                ("ms_dense", ct.c_double), ("ms_total", ct.c_double)]
+                ("ms_dense", ct.c_double), ("ms_total", ct.c_double), ("kernel_launches", ct.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -77,6 +78,7 @@ def lib() -> ct.CDLL:
         L.slrf_get_poles.argtypes = [vp, ct.POINTER(i), vp, vp]
         L.slrf_filter_apply.argtypes = [vp, vp, i, vp, vp]
         L.slrf_filter_stats.argtypes = [vp, vp, vp, vp]
+        L.slrf_filter_timing.argtypes = [vp, vp, i, vp, vp, vp, vp]
         L.slrf_rayleigh_ritz.argtypes = [vp, vp, i, vp, vp, i, i, vp, vp, vp]
         L.slrf_solve.argtypes = [vp, vp, i, ct.POINTER(i), vp, vp, vp, ct.POINTER(Stats)]
         L.slrf_solve_host.argtypes = [ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp, i, ct.POINTER(i), vp, vp, vp,
@@ -179,6 +181,19 @@ class Context:
         _check(lib().slrf_filter_apply(self.h, _ptr(X), k, _ptr(th), _ptr(U)), "slrf_filter_apply")
         return U
 
+    def filter_timing(self, X: torch.Tensor, theta: torch.Tensor | None = None):
+        """Kernel-by-kernel CUDA-event timing of one filter apply (see slrf_filter_timing)."""
+        X = _dev(X, torch.float64)
+        k = X.shape[1]
+        U = torch.empty_like(X)
+        th = None if theta is None else _dev(theta, torch.float64)
+        ms = np.zeros(4)
+        cnt = np.zeros(2, dtype=np.int32)
+        _check(lib().slrf_filter_timing(self.h, _ptr(X), k, _ptr(th), _ptr(U), _ptr(ms), _ptr(cnt)),
+               "slrf_filter_timing")
+        return {"ms_total": ms[0], "ms_spmm": ms[1], "ms_update": ms[2], "ms_init": ms[3],
+                "n_spmm": int(cnt[0]), "n_update": int(cnt[1]), "U": U}
+
     def filter_stats(self, k: int):
         m = self.opts.m
         it = np.zeros(m * k, dtype=np.int32)
@@ -259,6 +274,7 @@ class SlrfEigsh(torch.autograd.Function):
         ctx = Context(rowptr, col, valA.detach(), valB.detach(), gamma, block_L, opts)
         _, nf, ev, X, rs, _ = ctx.solve(V0)
         fctx.slrf = ctx
+        fctx.devices = (valA.device, valB.device)
         fctx.save_for_backward(ev, X)
         fctx.mark_non_differentiable(X)
         return ev.clone(), X.clone()
@@ -267,4 +283,4 @@ class SlrfEigsh(torch.autograd.Function):
     def backward(fctx, g_ev, g_X):
         ev, X = fctx.saved_tensors
         gA, gB = fctx.slrf.eig_grad(ev, X, g_ev.contiguous())
-        return gA, gB, None, None, None, None, None, None
+        return gA.to(fctx.devices[0]), gB.to(fctx.devices[1]), None, None, None, None, None, None

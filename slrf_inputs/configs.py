@@ -58,14 +58,33 @@ def bar1d(n: int = 2000, gamma: float | None = None, block: int = 32, m: int = 8
     return Workload(f"bar1d_{n}", p, gamma, block, m, seed, it_max, 20 if n == 2000 else None)
 
 
-def q1_lap(nodes: int = 41, gamma: float | None = None, block: int = 160, m: int = 8, seed: int = 2,
+def q1_lap_interval(nodes: int, want: int, shift: float = 1e-3):
+    """gamma for the Q1 Neumann Laplacian on nodes^3 nodes (unit cube): the midpoint of the
+    spectral gap nearest to `want` eigenvalues, from the tensor-product spectrum
+    lambda_abc = mu_a + mu_b + mu_c + shift with the 1D FEM values
+    mu_k = 6 (1 - cos(k pi/(nodes-1))) / (h^2 (2 + cos(k pi/(nodes-1)))), h = 1/(nodes-1).
+    Returns (gamma, count)."""
+    h = 1.0 / (nodes - 1)
+    c = np.cos(np.arange(nodes) * np.pi / (nodes - 1))
+    mu = 6.0 * (1.0 - c) / (h * h * (2.0 + c))
+    lam = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel()) + shift
+    gaps = np.nonzero(np.diff(lam) > 1e-6 * lam[1:])[0]
+    g = gaps[np.argmin(np.abs(gaps + 1 - want))]
+    return 0.5 * (lam[g] + lam[g + 1]), int(g + 1)
+
+
+def q1_lap(nodes: int = 41, gamma: float | None = None, block: int | None = None, m: int = 8, seed: int = 2,
            it_max: int = 40) -> Workload:
     p = fem.q1_scalar((nodes, nodes, nodes), shift=1e-3)
+    count = None
     if gamma is None:
-        if nodes != 41:
-            raise ValueError("give gamma for nodes != 41")
-        gamma = 259.0666
-    return Workload(f"q1_lap_{nodes}", p, gamma, block, m, seed, it_max, 105 if nodes == 41 else None)
+        if nodes == 41:
+            gamma, count = 259.0666, 105
+        else:
+            gamma, count = q1_lap_interval(nodes, 100)
+    if block is None:
+        block = 160 if nodes == 41 else int(np.ceil(1.5 * (count or 100)))
+    return Workload(f"q1_lap_{nodes}", p, gamma, block, m, seed, it_max, count)
 
 
 def q1_elast(nodes=(64, 64, 32), gamma: float | None = None, block: int = 480, m: int = 8, seed: int = 3,

@@ -1,0 +1,141 @@
+"""Parity of the CUDA filter apply (a1-a5) with the FP64 oracle, through the C ABI.
+
+Tolerances.  Poles are copied exactly; weights come from normal equations whose
+condition number is ~1e7, so they agree to ~1e-8.  U after a truncated COCG run depends
+on the rounding order of the SpMM sums and reductions; the CUDA path carries q = A p by
+the recurrence q = A r + beta q and solves in correction form, so its iterates differ
+from the oracle's by rounding amplified through It_max steps: measured <= 2.3e-9
+relative to max|U| across m = 1..16; the tests allow 1e-8.  COCG update counts must
+be identical.  The mixed path (complex-FP32 inner solve) is compared with the FP64
+oracle at FP32 accuracy times the filter's weight growth (sum |w_j| ~ 20): 5e-3.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+import pins
+import slrf_inputs as si
+from gpu_common import rel, slrf_mod  # noqa: F401
+from oracle import slrf_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+N, L = 500, 13  # 13 columns: ragged against the 4-column (m = 8) warp tile
+
+
+@pytest.fixture(scope="module")
+def bar():
+    p = si.bar1d_pencil(N)
+    lam = pins.bar1d_eigs(N)
+    gamma = 0.5 * (lam[7] + lam[8])
+    return p, lam, gamma
+
+
+@pytest.mark.parametrize("m", [8, 3, 1, 16])
+def test_poles_match_oracle(slrf_mod, bar, m):
+    p, lam, gamma = bar
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, slrf_mod.slrf_opts_default(m=m))
+    s, w = ctx.poles()
+    so, wo = orc.slrf_poles(m, gamma)
+    assert rel(s, so) <= 1e-14
+    assert rel(w, wo) <= 1e-7
+    ctx.close()
+
+
+@pytest.mark.parametrize("m,it", [(8, 60), (3, 40), (1, 30), (16, 20)])
+@pytest.mark.parametrize("warm", [False, True])
+def test_filter_apply_parity(slrf_mod, bar, m, it, warm):
+    p, lam, gamma = bar
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, slrf_mod.slrf_opts_default(m=m, it_max=it))
+    V1 = si.start_block(N, L, 5)
+    th = np.linspace(0.1, 1.5, L) * gamma if warm else None
+    U = ctx.filter_apply(torch.from_numpy(V1), None if th is None else torch.from_numpy(th)).cpu().numpy()
+    its, rr, bk = ctx.filter_stats(L)
+    so, wo = orc.slrf_poles(m, gamma)
+    Uo, fo = orc.filter_apply(p.A(), p.B(), V1, th, so, wo, it, 1e-10)
+    assert rel(U, Uo) <= 1e-8
+    assert np.array_equal(its, fo.iters)
+    assert np.abs(rr - fo.relres).max() <= 1e-8
+    assert not bk.any()
+    ctx.close()
+
+
+def test_filter_on_exact_eigenvectors(slrf_mod):
+    """Sec. 2: the filter maps an eigenvector x with eigenvalue lambda to Phi(lambda) x; with the
+    warm start at theta = lambda the initial residual vanishes and no COCG step is taken."""
+    p = si.q1_scalar((6, 5, 4), shift=1e-3)
+    lam, X = sla.eigh(p.A().toarray(), p.B().toarray())
+    gamma = 0.5 * (lam[9] + lam[10])
+    k = 14
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, k, slrf_mod.slrf_opts_default(it_max=300))
+    so, wo = orc.slrf_poles(8, gamma)
+    ref = X[:, :k] * orc.filter_value(lam[:k], so, wo)[None, :]
+    U = ctx.filter_apply(torch.from_numpy(np.ascontiguousarray(X[:, :k])),
+                         torch.from_numpy(lam[:k].copy())).cpu().numpy()
+    assert rel(U, ref) <= 1e-9
+    ctx.close()
+
+
+def test_conjugate_pole_table_gives_the_same_filter(slrf_mod, bar):
+    """A user pole table: poles conj(sigma_j) with weights conj(w_j) describe the same real
+    filter (Sec. 2, sigma_{N+j} = conj(sigma_j)), so U must not change."""
+    p, lam, gamma = bar
+    so, wo = orc.slrf_poles(8, gamma)
+    V1 = torch.from_numpy(si.start_block(N, L, 6))
+    c1 = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, slrf_mod.slrf_opts_default(it_max=50))
+    c2 = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L,
+                          slrf_mod.slrf_opts_default(it_max=50, poles=np.conj(so), weights=np.conj(wo)))
+    U1 = c1.filter_apply(V1).cpu().numpy()
+    U2 = c2.filter_apply(V1).cpu().numpy()
+    assert rel(U2, U1) <= 1e-9
+    c1.close()
+    c2.close()
+
+
+def test_mixed_precision_filter_close_to_fp64_oracle(slrf_mod, bar):
+    p, lam, gamma = bar
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L,
+                           slrf_mod.slrf_opts_default(it_max=60, precision=1))
+    V1 = si.start_block(N, L, 5)
+    so, wo = orc.slrf_poles(8, gamma)
+    U = ctx.filter_apply(torch.from_numpy(V1)).cpu().numpy()
+    Uo, _ = orc.filter_apply(p.A(), p.B(), V1, None, so, wo, 60, 1e-10)
+    assert rel(U, Uo) <= 5e-3
+    its, rr, bk = ctx.filter_stats(L)
+    assert not bk.any()
+    ctx.close()
+
+
+def test_cocg_breakdown_is_flagged_on_the_device(slrf_mod):
+    """M = diag(1, -1) (pole 0 on a 2x2 pencil with B = I) and b = (1, 1): p^T M p = 0 on the
+    first step; the column stops with its breakdown flag, exactly as in the oracle."""
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([0, 1], dtype=np.int32)
+    valA = np.array([1.0, -1.0])
+    valB = np.array([1.0, 1.0])
+    ctx = slrf_mod.Context(rowptr, col, valA, valB, 1.0, 1,
+                           slrf_mod.slrf_opts_default(m=1, it_max=10, poles=np.array([0j]),
+                                                      weights=np.array([1.0 + 0j])))
+    U = ctx.filter_apply(torch.ones(2, 1, dtype=torch.float64)).cpu().numpy()
+    its, rr, bk = ctx.filter_stats(1)
+    assert bk[0, 0] and its[0, 0] == 0
+    assert np.all(U == 0)
+    ctx.close()
+
+
+def test_full_size_sampled_columns(slrf_mod):
+    """41^3 Q1 Laplacian (n = 68,921): the GPU filter apply of the whole 160-column start
+    block, compared on sampled columns that the oracle solves one by one (columns are
+    independent systems)."""
+    wl = si.q1_lap(41)
+    p = wl.pencil
+    it = 40
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, slrf_mod.slrf_opts_default(it_max=it))
+    V1 = si.start_block(p.n, wl.block, wl.seed)
+    U = ctx.filter_apply(torch.from_numpy(V1)).cpu().numpy()
+    so, wo = orc.slrf_poles(8, wl.gamma)
+    cols = [0, 77, 159]
+    Uo, _ = orc.filter_apply(p.A(), p.B(), V1[:, cols], None, so, wo, it, 1e-10)
+    assert rel(U[:, cols], Uo) <= 1e-8
+    ctx.close()

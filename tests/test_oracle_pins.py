@@ -257,3 +257,34 @@ def test_sturm_count_matches_dense():
         c = pins.sturm_count(np.full(n, 2 / h), np.full(n - 1, -1 / h), gamma,
                              np.full(n, 4 * h / 6), np.full(n - 1, h / 6))
         assert c == pins.dense_inertia_count(p.A(), p.B(), gamma) == np.sum(pins.bar1d_eigs(n) < gamma)
+
+
+# ---------------------------------------------------------------- a12: eigenvalue adjoint
+def test_eig_grad_matches_finite_differences():
+    """Central differences of the dense generalized eigenvalues along random symmetric
+    directions on the pattern match the adjoint, for A and for B."""
+    E = np.exp(np.random.default_rng(4).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    Ad, Bd = p.A().toarray(), p.B().toarray()
+    lam, Xf = sla.eigh(Ad, Bd)
+    k = 6
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(k)
+    gA, gB = orc.eig_grad_values(p.rowptr, p.col, lam[:k], Xf[:, :k], g)
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    for _ in range(3):
+        S = np.zeros((p.n, p.n))
+        S[rows, p.col] = rng.standard_normal(p.nnz)
+        Dd = S + S.T  # symmetric, on the (symmetric) pattern
+        dvals = Dd[rows, p.col]
+        for M0, grad, other in ((Ad, gA, "A"), (Bd, gB, "B")):
+            h = 1e-6 * np.abs(M0).max() / np.abs(Dd).max()
+            if other == "A":
+                lp = sla.eigh(Ad + h * Dd, Bd, eigvals_only=True)[:k]
+                lm = sla.eigh(Ad - h * Dd, Bd, eigvals_only=True)[:k]
+            else:
+                lp = sla.eigh(Ad, Bd + h * Dd, eigvals_only=True)[:k]
+                lm = sla.eigh(Ad, Bd - h * Dd, eigvals_only=True)[:k]
+            fd = g @ (lp - lm) / (2 * h)
+            pred = grad @ dvals
+            assert abs(fd - pred) <= 1e-5 * abs(fd), (other, fd, pred)
