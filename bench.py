@@ -40,7 +40,7 @@ def workload(name: str, it_max: int | None):
 
     if name == "q1_lap_41":
         wl = si.q1_lap(41)
-        wl.it_max = it_max or 20
+        wl.it_max = it_max or 10
         desc = ("3D Q1 Laplacian + consistent mass, 41^3 nodes (n=68,921, 27 nnz/row), Neumann + 1e-3 B, "
                 "gamma=259.0666 (105 eigenpairs), block 160, m=8")
     elif name.startswith("q1_lap_"):
@@ -155,7 +155,7 @@ def main():
     ap.add_argument("--it-max", type=int, default=None)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mixed-it-max", type=int, default=30,
+    ap.add_argument("--mixed-it-max", type=int, default=15,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
     args = ap.parse_args()
 

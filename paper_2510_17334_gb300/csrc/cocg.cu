@@ -112,7 +112,7 @@ __device__ bool block_then_grid_reduce(double (&acc)[VEC][NQ], const int W, cons
 // ------------------------------------------------------------------------------ init
 // r0 = c g, p0 = r0, q0 = c (A g - sigma B g); reduce mu0 = p0^T q0, rho0 = r0^T r0, ||r0||^2.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R> a) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -136,11 +136,12 @@ __global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a
     }
     cf[v] = to_c<R>(c);
   }
-  double acc[VEC][kNQ];
+  constexpr int NQ = 5;
+  R acc[VEC][NQ];  // per-thread partial sums in the working precision
 #pragma unroll
   for (int v = 0; v < VEC; ++v)
 #pragma unroll
-    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+    for (int qq = 0; qq < NQ; ++qq) acc[v][qq] = R(0);
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   for (int64_t i = i0 + warp; i < i1; i += kWarps) {
@@ -156,20 +157,25 @@ __global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a
       C t; t.x = agv - sg[v].x * bgv; t.y = -sg[v].y * bgv;
       C q0 = cmul(cf[v], t);
       rv.z[v] = r0; qv.z[v] = q0;
-      acc[v][0] += (double)(r0.x * q0.x - r0.y * q0.y);
-      acc[v][1] += (double)(r0.x * q0.y + r0.y * q0.x);
-      acc[v][2] += (double)(r0.x * r0.x - r0.y * r0.y);
-      acc[v][3] += (double)(2 * r0.x * r0.y);
-      acc[v][4] += (double)(r0.x * r0.x + r0.y * r0.y);
+      acc[v][0] += r0.x * q0.x - r0.y * q0.y;
+      acc[v][1] += r0.x * q0.y + r0.y * q0.x;
+      acc[v][2] += r0.x * r0.x - r0.y * r0.y;
+      acc[v][3] += 2 * r0.x * r0.y;
+      acc[v][4] += r0.x * r0.x + r0.y * r0.y;
     }
     const size_t off = (size_t)i * a.W + w0;
     stv<R>(a.r + off, rv);
     stv<R>(a.p + off, rv);
     stv<R>(a.q + off, qv);
   }
-  double out[kNQ];
+  double out[NQ];
   int w;
-  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+  double accd[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
+  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
     return;
   if (threadIdx.x < 32 * VEC) {
     WScal s = a.ws[w];
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) cocg_init_kernel(const CocgArgs<R> a
 // d += alpha p (d = alpha p on the first step); r -= alpha q; reduce rho' and ||r||^2.
 // With final_acc, also U[i][c] = coefV[c] V[i][c] + sum_j 2 Re(w_j d_j).
 template <typename R, bool FIRST, bool FINAL>
-__global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs<R> a) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -209,11 +215,12 @@ __global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R>
     al[v] = to_c<R>(s.alpha);
     wt[v] = to_c<R>(a.wt[(w0 + v) & (a.mp - 1)]);
   }
-  double acc[VEC][kNQ];
+  constexpr int NQ = 3;
+  R acc[VEC][NQ];  // per-thread partial sums in the working precision
 #pragma unroll
   for (int v = 0; v < VEC; ++v)
 #pragma unroll
-    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+    for (int qq = 0; qq < NQ; ++qq) acc[v][qq] = R(0);
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   const int lanes_per_col = a.mp >= VEC ? a.mp / VEC : 1;
@@ -235,9 +242,9 @@ __global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R>
           rv.z[v] = cfms(al[v], qv.z[v], rv.z[v]);
         }
         const C rr = rv.z[v];
-        acc[v][0] += (double)(rr.x * rr.x - rr.y * rr.y);
-        acc[v][1] += (double)(2 * rr.x * rr.y);
-        acc[v][2] += (double)(rr.x * rr.x + rr.y * rr.y);
+        acc[v][0] += rr.x * rr.x - rr.y * rr.y;
+        acc[v][1] += 2 * rr.x * rr.y;
+        acc[v][2] += rr.x * rr.x + rr.y * rr.y;
       }
       stv<R>(a.r + off, rv);
     }
@@ -269,9 +276,14 @@ __global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R>
       }
     }
   }
-  double out[kNQ];
+  double out[NQ];
   int w;
-  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+  double accd[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
+  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
     return;
   if (threadIdx.x < 32 * VEC) {
     WScal s = a.ws[w];
@@ -297,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) cocg_update_kernel(const CocgArgs<R>
 // ------------------------------------------------------------------------------ spmm
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) cocg_spmm_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R> a) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -317,11 +329,12 @@ __global__ void __launch_bounds__(kThreads) cocg_spmm_kernel(const CocgArgs<R> a
   }
   // warp-uniform: skip the tile's SpMM when no column in it is still iterating
   const bool warp_act = __any_sync(0xffffffffu, any_act);
-  double acc[VEC][kNQ];
+  constexpr int NQ = 2;
+  R acc[VEC][NQ];  // per-thread partial sums in the working precision
 #pragma unroll
   for (int v = 0; v < VEC; ++v)
 #pragma unroll
-    for (int qq = 0; qq < kNQ; ++qq) acc[v][qq] = 0.0;
+    for (int qq = 0; qq < NQ; ++qq) acc[v][qq] = R(0);
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   if (warp_act) {
@@ -359,16 +372,21 @@ __global__ void __launch_bounds__(kThreads) cocg_spmm_kernel(const CocgArgs<R> a
         const C qn = cfma(be[v], qv.z[v], s);
         pv.z[v] = pn;
         qv.z[v] = qn;
-        acc[v][0] += (double)(pn.x * qn.x - pn.y * qn.y);
-        acc[v][1] += (double)(pn.x * qn.y + pn.y * qn.x);
+        acc[v][0] += pn.x * qn.x - pn.y * qn.y;
+        acc[v][1] += pn.x * qn.y + pn.y * qn.x;
       }
       stv<R>(a.p + off, pv);
       stv<R>(a.q + off, qv);
     }
   }
-  double out[kNQ];
+  double out[NQ];
   int w;
-  if (!block_then_grid_reduce<VEC, kNQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+  double accd[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
+  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
     return;
   if (threadIdx.x < 32 * VEC) {
     WScal s = a.ws[w];

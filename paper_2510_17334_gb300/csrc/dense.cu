@@ -309,9 +309,11 @@ void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cud
 
 // ------------------------------------------------------------------------------ Jacobi
 // Two-sided cyclic Jacobi with the round-robin (circle) ordering, which makes the kk/2
-// rotations of one round disjoint.  Block b owns pair b of every round: it computes the
-// rotation (phase 1), then, after a grid barrier, rewrites the two rows p, q of
-// J^T A J and the two rows p, q of V^T (phase 2).  A sweep with no rotation ends the loop.
+// rotations of one round disjoint.  Every block computes all rotations of the round
+// (cheap 2x2 problems), then rewrites the rows p, q of J^T A J and of V^T for the pairs
+// it owns; one grid barrier per round.  The sweep loop stops once the largest relative
+// off-diagonal met in a sweep is below 1e-8 (quadratic convergence leaves it at rounding
+// level after that sweep).
 __device__ __forceinline__ void rr_pair(int kk, int r, int b, int &p, int &q) {
   const int M = kk - 1;
   int a0, a1;
@@ -339,34 +341,46 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
     A[t] = (i < k && j < k) ? H[(size_t)i * ldh + j] : 0.0;
     Vt[t] = (i == j) ? 1.0 : 0.0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) { w.flags[0] = 0; w.flags[1] = 0; }
   if (!grid_sync(gb, nb)) return;
   __shared__ double rp[512], rq[512];  // kk <= 512
+  __shared__ double cs[512][2];        // rotation (c, s) of every index for this round
+  __shared__ double red[128];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // largest |a_pq| / sqrt(|a_pp a_qq|) met this sweep; identical in every block
+    double off_max = 0.0;
     for (int r = 0; r < kk - 1; ++r) {
-      for (int b = blockIdx.x; b < kk / 2; b += nb) {
+      // every block computes every rotation of the round (kk/2 independent 2x2 problems),
+      // so no barrier is needed between the rotation and the update phase
+      double my_off = 0.0;
+      for (int b = threadIdx.x; b < kk / 2; b += blockDim.x) {
         int p, q;
         rr_pair(kk, r, b, p, q);
-        if (threadIdx.x == 0) {
-          const double app = __ldcg(&A[(size_t)p * kk + p]), aqq = __ldcg(&A[(size_t)q * kk + q]),
-                       apq = __ldcg(&A[(size_t)p * kk + q]);
-          double c = 1.0, s = 0.0;
-          if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-            w.flags[sweep & 1] = 1;
-          }
-          w.rot[3 * p] = c; w.rot[3 * p + 1] = s; w.rot[3 * p + 2] = 1.0;  // p is first of its pair
-          w.rot[3 * q] = c; w.rot[3 * q + 1] = s; w.rot[3 * q + 2] = 0.0;
+        const double app = __ldcg(&A[(size_t)p * kk + p]), aqq = __ldcg(&A[(size_t)q * kk + q]),
+                     apq = __ldcg(&A[(size_t)p * kk + q]);
+        double c = 1.0, sn = 0.0;
+        const double scale = sqrt(fabs(app * aqq));
+        const double rel = scale > 0.0 ? fabs(apq) / scale : (apq != 0.0 ? 1.0 : 0.0);
+        my_off = fmax(my_off, rel);
+        if (apq != 0.0 && fabs(apq) > 1e-15 * scale) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          sn = t * c;
         }
+        cs[p][0] = c; cs[p][1] = sn;
+        cs[q][0] = c; cs[q][1] = sn;
       }
-      if (!grid_sync(gb, nb)) return;
+      red[threadIdx.x] = my_off;
+      __syncthreads();
+      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+      }
+      off_max = fmax(off_max, red[0]);
       for (int b = blockIdx.x; b < kk / 2; b += nb) {
         int p, q;
         rr_pair(kk, r, b, p, q);
-        const double c = __ldcg(&w.rot[3 * p]), s = __ldcg(&w.rot[3 * p + 1]);
+        const double c = cs[p][0], sn = cs[p][1];
         for (int x = threadIdx.x; x < kk; x += blockDim.x) {
           rp[x] = __ldcg(&A[(size_t)p * kk + x]);
           rq[x] = __ldcg(&A[(size_t)q * kk + x]);
@@ -374,33 +388,29 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
         __syncthreads();
         for (int x = threadIdx.x; x < kk; x += blockDim.x) {
           const int y = rr_partner(kk, r, x);
-          const double c2 = __ldcg(&w.rot[3 * x]), s2 = __ldcg(&w.rot[3 * x + 1]);
-          const bool first = __ldcg(&w.rot[3 * x + 2]) != 0.0;
+          const double c2 = cs[x][0], s2 = cs[x][1];
+          const bool first = x < y;  // the smaller index is p of its pair
           // (A J)[row][x] for rows p and q
           double ajp, ajq;
           if (first) { ajp = c2 * rp[x] - s2 * rp[y]; ajq = c2 * rq[x] - s2 * rq[y]; }
           else { ajp = s2 * rp[y] + c2 * rp[x]; ajq = s2 * rq[y] + c2 * rq[x]; }
-          double np = c * ajp - s * ajq, nq = s * ajp + c * ajq;
+          double np = c * ajp - sn * ajq, nq = sn * ajp + c * ajq;
           if (x == q) np = 0.0;  // annihilated entry
           if (x == p) nq = 0.0;
           A[(size_t)p * kk + x] = np;
           A[(size_t)q * kk + x] = nq;
           const double vp = __ldcg(&Vt[(size_t)p * kk + x]), vq = __ldcg(&Vt[(size_t)q * kk + x]);
-          Vt[(size_t)p * kk + x] = c * vp - s * vq;
-          Vt[(size_t)q * kk + x] = s * vp + c * vq;
+          Vt[(size_t)p * kk + x] = c * vp - sn * vq;
+          Vt[(size_t)q * kk + x] = sn * vp + c * vq;
         }
         __syncthreads();
       }
       if (!grid_sync(gb, nb)) return;
     }
-    // sweep done: stop when no rotation happened
-    const int rotated = *(volatile int *)&w.flags[sweep & 1];
-    if (!grid_sync(gb, nb)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.flags[sweep & 1] = 0;
-    if (rotated == 0) break;
-    if (!grid_sync(gb, nb)) return;
+    // quadratic convergence: once every off-diagonal met in a sweep is below 1e-8 of its
+    // diagonal scale, the rotations of that sweep leave them at rounding level
+    if (off_max < 1e-8) break;
   }
-  if (!grid_sync(gb, nb)) return;
   // sort ascending (stable by index) and write theta, S (column i = eigenvector i)
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) {

@@ -198,6 +198,8 @@ __global__ void final_gather_kernel(int64_t n, int nconv, int cnt, const int *ra
 // ----------------------------------------------------------------------------- filter
 // U = sum_j 2 Re(w_j Y_j), (A - sigma_j B) Y_j = B X, in correction form (see cocg.cu).
 // AXp/BXp: A X and B X if already known (warm start), else computed here.
+constexpr int64_t kRowBlocks = 152 * 4;
+
 // Optional per-kernel timing of one filter apply (measurement hook, direct launches).
 struct FilterTiming {
   double ms_init = 0, ms_spmm = 0, ms_update = 0;
@@ -210,10 +212,10 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   const int vec = cocg_vec<R>();
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
-  const int ntiles = W / (32 * vec);
-  // rows per block: enough blocks to fill the GPU about 8 deep, at least 16 rows each
-  int64_t target = std::max<int64_t>(1, (152 * 8 + ntiles - 1) / ntiles);
-  int64_t rpb = std::max<int64_t>(16, (ctx->n + target - 1) / target);
+  // Row blocks per tile: about as many as the GPU holds resident (152 SMs x 4 blocks), so
+  // that the blocks in flight at any time all belong to one or two tiles (the tile index
+  // varies slowest) and the gathered rows of those tiles stay in L2.
+  const int64_t rpb = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
   const int nrb = (int)((ctx->n + rpb - 1) / rpb);
   CocgArgs<R> a{};
   a.n = ctx->n;
@@ -338,34 +340,44 @@ static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
 }
 
 // ----------------------------------------------------------------------------- RR step
-// U (n x k, ld L) -> B-orth vs X (CGS2) -> CholQR2 -> Rayleigh-Ritz -> Vt, AVt, BVt,
-// theta, res, res_paper, sgn.  Chol failure is reported through iflags[4].
-static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const double *BX, int nconv, int ldx) {
+// U (n x k, ld L) -> B-orth vs X (CGS2) -> Cholesky-QR2 -> Rayleigh-Ritz -> Vt, AVt, BVt,
+// theta, res, res_paper, sgn.  The second CholQR pass is folded into the projection:
+//   U1 = U R1^{-1};  G2 = U1^T B U1 = R2^T R2;  H = R2^{-T} (U1^T A U1) R2^{-1} = S Theta S^T;
+//   V = U1 (R2^{-1} S)
+// which equals projecting on U2 = U1 R2^{-1} without forming U2 (one n x k^2 product and
+// one SpMM fewer).  With want_basis, U2 is formed into U as well.  Cholesky failure is
+// reported through iflags[4].
+static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const double *BX, int nconv, int ldx,
+                   bool want_basis = false) {
   const cudaStream_t st = ctx->st;
   const int64_t n = ctx->n;
   const int L = ctx->L;
-  ctx->launches += (nconv > 0 ? 6 : 0) + 10 + 8;
+  ctx->launches += (nconv > 0 ? 6 : 0) + 19 + (want_basis ? 1 : 0);
   if (nconv > 0) {
     for (int pass = 0; pass < 2; ++pass) {
       gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st);
       gemm_nn(n, X, ldx, nconv, ctx->Wm, k, k, U, L, -1.0, 1.0, false, st);
     }
   }
-  double *cur = U, *nxt = ctx->U2;
-  for (int pass = 0; pass < 2; ++pass) {
-    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, cur, L, k, nullptr, ctx->BU, L, st);
-    gram(n, cur, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
-    chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4 + pass * 0, st);
-    gemm_nn(n, cur, L, k, ctx->Rinv, k, k, nxt, L, 1.0, 0.0, true, st);
-    std::swap(cur, nxt);
-  }
-  // cur holds the B-orthonormal basis (== U after two swaps)
-  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, cur, L, k, ctx->BU, nullptr, L, st);
-  gram(n, cur, L, k, ctx->BU, L, k, ctx->Hm, k, true, ctx->work, st);
+  double *U1 = ctx->U2, *AU1 = ctx->AG;
+  // pass 1: U1 = U R1^{-1}
+  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st);
+  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
+  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st);
+  gemm_nn(n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true, st);
+  // pass 2 and projection
+  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U1, L, k, AU1, ctx->BU, L, st);
+  gram(n, U1, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
+  gram(n, U1, L, k, AU1, L, k, ctx->Hm, k, true, ctx->work, st);
+  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st);
+  gemm_nn(k, ctx->Hm, k, k, ctx->Rinv, k, k, ctx->Wm, k, 1.0, 0.0, true, st);  // T = H1 R2^{-1}
+  gram(k, ctx->Rinv, k, k, ctx->Wm, k, k, ctx->Gm, k, true, ctx->work, st);       // H = R2^{-T} T
   CKL();
-  int rc = jacobi_eig(k, ctx->Hm, k, ctx->theta, ctx->Sm, k, ctx->jw, st);
+  int rc = jacobi_eig(k, ctx->Gm, k, ctx->theta, ctx->Sm, k, ctx->jw, st);
   if (rc != SLRF_OK) { ctx->status = rc; return rc; }
-  gemm_nn(n, cur, L, k, ctx->Sm, k, k, ctx->Vt, L, 1.0, 0.0, false, st);
+  gemm_nn(k, ctx->Rinv, k, k, ctx->Sm, k, k, ctx->Wm, k, 1.0, 0.0, false, st);  // Z = R2^{-1} S
+  gemm_nn(n, U1, L, k, ctx->Wm, k, k, ctx->Vt, L, 1.0, 0.0, false, st);         // V = U1 Z
+  if (want_basis) gemm_nn(n, U1, L, k, ctx->Rinv, k, k, U, L, 1.0, 0.0, true, st);
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
   ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
   CKL();
@@ -474,8 +486,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   const size_t csz = ctx->mixed ? 8 : 16;
   const size_t state = 4 * (size_t)n * ctx->Wmax * csz;
   const size_t ntiles_max = ctx->Wmax / (32 * ctx->vec);
-  // run_cocg uses nrb <= ceil(1216 / ntiles) row blocks, so nrb * W <= (1216 + ntiles) * 32 * vec
-  const size_t partial = (152 * 8 + ntiles_max + 1) * 32 * (size_t)ctx->vec * kNQ;
+  // run_cocg uses at most kRowBlocks row blocks for any k <= L
+  const size_t partial = (size_t)kRowBlocks * ctx->Wmax * kNQ;
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
   const size_t need = (state + blocks + matrix) + 8 * partial + (64u << 20);
@@ -680,7 +692,7 @@ int slrf_rayleigh_ritz(slrf_ctx *ctx, double *U, int k, const double *X, const d
     copy_block(n, n_conv, BX, ldx, ctx->BX, L, ctx->st);
   }
   CK(cudaMemsetAsync(ctx->iflags + 4, 0, sizeof(int), ctx->st));
-  int rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, n_conv, L);
+  int rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, n_conv, L, true);
   if (rc != SLRF_OK) return rc;
   int hf[16];
   CK(cudaMemcpyAsync(hf, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
