@@ -190,6 +190,33 @@ int slrf_solve_host(const slrf_csr_pair *pencil_host, double gamma, int block_L,
 int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, int ldx,
                   const double *g_eval, const double *g_X, double *gA, double *gB);
 
+/* Size of the static device array that slrf_filter_apply_static works in (per GPU). */
+#define SLRF_STATIC_ARENA_BYTES (64u << 20)
+
+/* Allocation-free filter apply.  The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory -- code running under another framework's
+ * memory pool or budget, or a plugin that must not call cudaMalloc once it has started.
+ * It computes exactly what slrf_filter_apply computes in FP64 (opts->precision must be 0),
+ * but without a context: pencil (device pointers, used in place, not copied), gamma,
+ * opts (HOST, NULL = defaults; a user pole table is honoured), X (device n x k),
+ * theta (device, k entries, or NULL for the zero initial guess), U (device n x k,
+ * output), stream (a cudaStream_t or NULL): all work is enqueued on that stream.
+ * Every scratch buffer lives in one static device array of SLRF_STATIC_ARENA_BYTES
+ * (64 MiB) that each GPU which loads the library holds until the process exits; a call
+ * whose working set -- about 64 n W + 24 n k bytes, W = k m rounded up to a multiple of
+ * 32 -- does not fit returns SLRF_EINVAL before any device work (the 1D bar with
+ * n = 2000, k = 32, m = 8 uses 36 MB).  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  The array keeps the previous call's contents and the call clears
+ * what must start at zero; every call shares the one array, so calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Synchronises the stream once, after setting up the pole table.
+ * Errors: SLRF_EINVAL (NULL or inconsistent arguments, precision != 0, too large),
+ * SLRF_ECUDA. */
+int slrf_filter_apply_static(const slrf_csr_pair *pencil, double gamma, const slrf_opts *opts,
+                             const double *X, int k, const double *theta, double *U, void *stream);
+
 /* Release the context and all its device memory.  NULL is accepted. */
 void slrf_destroy(slrf_ctx *ctx);
 

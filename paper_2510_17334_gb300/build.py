@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libslrf.so")
-SOURCES = ["cocg.cu", "dense.cu", "adjoint.cu", "slrf.cu"]
+SOURCES = ["cocg.cu", "dense.cu", "adjoint.cu", "slrf.cu", "static_filter.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -31,7 +31,7 @@ SLRF_ESTATE = -10
 SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_apply", "slrf_filter_timing",
            "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
-           "slrf_strerror", "slrf_last_error")
+           "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static")
 
 
 class SlrfError(RuntimeError):
@@ -84,6 +84,7 @@ def lib() -> ct.CDLL:
         L.slrf_solve_host.argtypes = [ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp, i, ct.POINTER(i), vp, vp, vp,
                                       ct.POINTER(Stats)]
         L.slrf_eig_grad.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp]
+        L.slrf_filter_apply_static.argtypes = [ct.POINTER(CsrPair), d, ct.POINTER(Opts), vp, i, vp, vp, vp]
         L.slrf_destroy.argtypes = [vp]
         L.slrf_destroy.restype = None
         L.slrf_strerror.argtypes = [i]
@@ -240,6 +241,20 @@ class Context:
         _check(lib().slrf_eig_grad(self.h, k, _ptr(evals), _ptr(X), k, _ptr(g), _ptr(gX), _ptr(gA), _ptr(gB)),
                "slrf_eig_grad")
         return gA, gB
+
+
+def filter_apply_static(rowptr, col, valA, valB, gamma, opts, X, theta=None, U=None, stream=None):
+    """slrf_filter_apply_static: the FP64 filter apply without a context or any device
+    allocation inside the library (device tensors in, U out; the caller's stream)."""
+    n = int(rowptr.numel() - 1)
+    k = int(X.shape[1])
+    if U is None:
+        U = torch.empty_like(X)
+    pair = CsrPair(n, int(col.numel()), _ptr(rowptr), _ptr(col), _ptr(valA), _ptr(valB))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().slrf_filter_apply_static(ct.byref(pair), float(gamma), ct.byref(opts), _ptr(X), k, _ptr(theta),
+                                          _ptr(U), ct.c_void_p(st.cuda_stream)), "slrf_filter_apply_static")
+    return U
 
 
 def slrf_solve_host(rowptr, col, valA, valB, gamma, block_L, opts=None, V0=None, cap=None):
