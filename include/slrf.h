@@ -64,7 +64,7 @@ typedef struct {
   double beta;            /* relaxation (Tikhonov) weight of the pole design, default 0.01  */
   double band;            /* stop band starts at band*gamma, default 1.3                    */
   int it_max;             /* It_max-linear: fixed COCG updates per solve (Alg. 2 l.10)     */
-  int refine_max;         /* mixed path: FP64 refinement steps, >= 1, default 1             */
+  int refine_max;         /* mixed path: refinement steps (FP64 residual + FP32 solve), >= 1 */
   int outer_max;          /* outer iteration cap, default 100                               */
   double tol_inner;       /* COCG stop ||r|| <= tol_inner ||r0||, default 1e-10 (Sec. 3.2)  */
   double tol_eig;         /* lock when ||Av - theta Bv|| / ||Av|| <= tol_eig, default 1e-8  */
@@ -121,7 +121,11 @@ int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w);
  * (device, k entries) gives the warm start y0 = x_c / (theta_c - sigma_j) (Alg. 2 l.21,
  * the Cayley form of the Proposition, Sec. 4); theta = NULL gives y0 = 0.  U (device,
  * n x k row-major) receives the filtered block and may not alias X.  Precision follows
- * opts.precision.  Asynchronous on the context stream.
+ * opts.precision: with precision = 1 the solve runs in FP64 iterative refinement --
+ * step 1 takes its FP64 residual from the real sweep, every further step (refine_max in
+ * all) computes R = B X - (A - sigma_j B) Y_j in FP64, solves for the correction with
+ * complex-FP32 COCG (FP32 accumulation) and adds it to Y_j in FP64.  Asynchronous on
+ * the context stream.
  * Errors: SLRF_EINVAL (k < 1 or k > L, NULL X or U), SLRF_ESTATE, SLRF_ECUDA. */
 int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U);
 

@@ -184,6 +184,8 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R
     s.r0n2 = out[4];
     s.rn2 = out[4];
     s.iters = 0;
+    s.iters_total = 0;
+    if (a.r00 != nullptr) a.r00[w] = out[4];
     s.brk = 0;
     s.beta = make_double2(0.0, 0.0);
     if (s.active && !(out[4] > 0.0)) s.active = 0;  // zero right-hand side: nothing to do
@@ -196,15 +198,17 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R
 // ------------------------------------------------------------------------------ update
 // d += alpha p (d = alpha p on the first step); r -= alpha q; reduce rho' and ||r||^2.
 // With final_acc, also U[i][c] = coefV[c] V[i][c] + sum_j 2 Re(w_j d_j).
-template <typename R, bool FIRST, bool FINAL>
+template <typename R, bool FIRST, int FM>
 __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs<R> a) {
+  constexpr bool FINAL = FM != kFinalNone;
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rb = blockIdx.x, tile = blockIdx.y;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
-  C al[VEC], wt[VEC];
+  C al[VEC];
+  double2 wt[VEC];  // weights stay FP64: the pole sum is formed in FP64
   bool act[VEC];
   bool any_act = false;
 #pragma unroll
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs
     act[v] = s.active != 0;
     any_act |= act[v];
     al[v] = to_c<R>(s.alpha);
-    wt[v] = to_c<R>(a.wt[(w0 + v) & (a.mp - 1)]);
+    wt[v] = a.wt[(w0 + v) & (a.mp - 1)];
   }
   constexpr int NQ = 3;
   R acc[VEC][NQ];  // per-thread partial sums in the working precision
@@ -249,12 +253,28 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs
       stv<R>(a.r + off, rv);
     }
     if (FIRST || any_act) stv<R>(a.d + off, dv);
-    if (FINAL) {
-      // U = coefV V + sum over this column's poles of 2 Re(w_j d_j)
+    if (FM == kFinalStoreD || FM == kFinalAddD) {
+      // refinement: accumulate this step's correction into the FP64 D
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        double2 acc2 = FM == kFinalAddD ? a.D64[off + v] : make_double2(0.0, 0.0);
+        acc2.x += (double)dv.z[v].x;
+        acc2.y += (double)dv.z[v].y;
+        a.D64[off + v] = acc2;
+      }
+    } else if (FINAL) {
+      // U = coefV V + sum over this column's poles of 2 Re(w_j y_j), y_j = d_j (+ D_j)
       double part[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v)
-        part[v] = 2.0 * ((double)wt[v].x * (double)dv.z[v].x - (double)wt[v].y * (double)dv.z[v].y);
+      for (int v = 0; v < VEC; ++v) {
+        double yr = (double)dv.z[v].x, yi = (double)dv.z[v].y;
+        if (FM == kFinalUFromD) {
+          const double2 dd = a.D64[off + v];
+          yr += dd.x;
+          yi += dd.y;
+        }
+        part[v] = 2.0 * (wt[v].x * yr - wt[v].y * yi);
+      }
       if (a.mp >= VEC) {
         double s = 0.0;
 #pragma unroll
@@ -289,6 +309,7 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs
     WScal s = a.ws[w];
     if (s.active) {
       s.iters += 1;
+      s.iters_total += 1;
       s.rn2 = out[2];
       const double2 rho_new = make_double2(out[0], out[1]);
       if (out[2] <= a.tol2 * s.r0n2) {
@@ -308,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs
 
 // ------------------------------------------------------------------------------ spmm
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
-template <typename R>
+template <typename R, bool FRESH>
 __global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R> a) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
@@ -364,12 +385,17 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R
         }
       }
       const size_t off = (size_t)i * a.W + w0;
-      Vec<R> rv = ldv<R>(a.r + off), pv = ldv<R>(a.p + off), qv = ldv<R>(a.q + off);
+      Vec<R> rv = ldv<R>(a.r + off), pv, qv;
+      if (!FRESH) {
+        pv = ldv<R>(a.p + off);
+        qv = ldv<R>(a.q + off);
+      }
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         const C s = cfms(sg[v], sb[v], sa[v]);  // A r - sigma B r
-        const C pn = cfma(be[v], pv.z[v], rv.z[v]);
-        const C qn = cfma(be[v], qv.z[v], s);
+        // a fresh start (refinement step) has p = r and q = (A - sigma B) r
+        const C pn = FRESH ? rv.z[v] : cfma(be[v], pv.z[v], rv.z[v]);
+        const C qn = FRESH ? s : cfma(be[v], qv.z[v], s);
         pv.z[v] = pn;
         qv.z[v] = qn;
         acc[v][0] += pn.x * qn.x - pn.y * qn.y;
@@ -404,6 +430,107 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R
   }
 }
 
+// ------------------------------------------------------------------------------ residual
+// Refinement step s >= 2 of the FP32 path: the FP64 residual of the accumulated correction
+//   R = r0 - (A - sigma B) D,   r0 = c_w gscale_c g,   D in FP64,
+// written as the new FP32 right-hand side r (p and q follow in the fresh SpMM); new
+// scalars rho = R^T R, ||R||^2 per w.  Every column with a nonzero residual (and no
+// earlier breakdown) is refined; its FP32 solve stops at tol ||R|| or It_max.
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
+  constexpr int VEC = cocg_vec<R>();
+  using C = cx_t<R>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rb = blockIdx.x, tile = blockIdx.y;
+  const int w_tile0 = tile * 32 * VEC;
+  const int w0 = w_tile0 + lane * VEC;
+  double2 sg[VEC], cf[VEC];
+  int cidx[VEC];
+  bool ok[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const int w = w0 + v;
+    sg[v] = a.sig64[w & (a.mp - 1)];
+    cidx[v] = w / a.mp;
+    ok[v] = cidx[v] < a.k;
+    double2 c = a.cfac[w];
+    if (a.gscale != nullptr && ok[v]) {
+      const double gs = a.gscale[cidx[v]];
+      c.x *= gs;
+      c.y *= gs;
+    }
+    cf[v] = c;
+  }
+  constexpr int NQ = 3;
+  double acc[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) acc[v][qq] = 0.0;
+  const int64_t i0 = (int64_t)rb * a.rows_per_block;
+  const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
+  for (int64_t i = i0 + warp; i < i1; i += kWarps) {
+    double2 sa[VEC], sb[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) { sa[v] = make_double2(0, 0); sb[v] = make_double2(0, 0); }
+    const int64_t rs = a.rowptr[i], re = a.rowptr[i + 1];
+    for (int64_t e0 = rs; e0 < re; e0 += 32) {
+      const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
+      int cl = 0;
+      double avl = 0, bvl = 0;
+      if (lane < cnt) { cl = a.col[e0 + lane]; avl = a.valA64[e0 + lane]; bvl = a.valB64[e0 + lane]; }
+      for (int t = 0; t < cnt; ++t) {
+        const int c = __shfl_sync(0xffffffffu, cl, t);
+        const double av = __shfl_sync(0xffffffffu, avl, t);
+        const double bv = __shfl_sync(0xffffffffu, bvl, t);
+        const double2 *xr = a.D64 + (size_t)c * a.W + w0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const double2 x = xr[v];
+          sa[v].x = fma(av, x.x, sa[v].x);
+          sa[v].y = fma(av, x.y, sa[v].y);
+          sb[v].x = fma(bv, x.x, sb[v].x);
+          sb[v].y = fma(bv, x.y, sb[v].y);
+        }
+      }
+    }
+    const size_t off = (size_t)i * a.W + w0;
+    Vec<R> rv;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      const double g = ok[v] ? a.g[(size_t)i * a.ldg + cidx[v]] : 0.0;
+      // r0 - (A D - sigma B D)
+      const double mdx = sa[v].x - (sg[v].x * sb[v].x - sg[v].y * sb[v].y);
+      const double mdy = sa[v].y - (sg[v].x * sb[v].y + sg[v].y * sb[v].x);
+      C r;
+      r.x = (R)(cf[v].x * g - mdx);
+      r.y = (R)(cf[v].y * g - mdy);
+      rv.z[v] = r;
+      const double rx = (double)r.x, ry = (double)r.y;
+      acc[v][0] += rx * rx - ry * ry;
+      acc[v][1] += 2.0 * rx * ry;
+      acc[v][2] += rx * rx + ry * ry;
+    }
+    stv<R>(a.r + off, rv);
+  }
+  double out[NQ];
+  int w;
+  if (!block_then_grid_reduce<VEC, NQ>(acc, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+    return;
+  if (threadIdx.x < 32 * VEC) {
+    WScal s = a.ws[w];
+    const bool valid = (w / a.mp) < a.k && (w & (a.mp - 1)) < a.m;
+    s.rho = make_double2(out[0], out[1]);
+    s.r0n2 = out[2];
+    s.rn2 = out[2];
+    s.iters = 0;
+    s.beta = make_double2(0.0, 0.0);
+    s.alpha = make_double2(0.0, 0.0);
+    s.active = (valid && s.brk == 0 && out[2] > 0.0) ? 1 : 0;
+    a.ws[w] = s;
+  }
+}
+
 // ------------------------------------------------------------------------------ prepare
 __global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
                                     const double *theta, double2 *cfac, double *coefV, WScal *ws) {
@@ -417,7 +544,7 @@ __global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *
   s.active = valid ? 1 : 0;
   s.iters = 0;
   s.brk = 0;
-  s.pad = 0;
+  s.iters_total = 0;
   ws[w] = s;
   double2 cf = make_double2(1.0, 0.0);
   if (theta != nullptr && valid) {
@@ -472,21 +599,42 @@ template <typename R> static dim3 grid_of(const CocgArgs<R> &a) {
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
   cocg_init_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
 }
-template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, bool final_acc, cudaStream_t st) {
-  if (first && final_acc) cocg_update_kernel<R, true, true><<<grid_of(a), kThreads, 0, st>>>(a);
-  else if (first) cocg_update_kernel<R, true, false><<<grid_of(a), kThreads, 0, st>>>(a);
-  else if (final_acc) cocg_update_kernel<R, false, true><<<grid_of(a), kThreads, 0, st>>>(a);
-  else cocg_update_kernel<R, false, false><<<grid_of(a), kThreads, 0, st>>>(a);
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st) {
+  const dim3 g = grid_of(a);
+#define UPD(F, M) cocg_update_kernel<R, F, M><<<g, kThreads, 0, st>>>(a)
+  if (first) {
+    switch (fm) {
+      case kFinalNone: UPD(true, kFinalNone); break;
+      case kFinalU: UPD(true, kFinalU); break;
+      case kFinalStoreD: UPD(true, kFinalStoreD); break;
+      case kFinalAddD: UPD(true, kFinalAddD); break;
+      default: UPD(true, kFinalUFromD); break;
+    }
+  } else {
+    switch (fm) {
+      case kFinalNone: UPD(false, kFinalNone); break;
+      case kFinalU: UPD(false, kFinalU); break;
+      case kFinalStoreD: UPD(false, kFinalStoreD); break;
+      case kFinalAddD: UPD(false, kFinalAddD); break;
+      default: UPD(false, kFinalUFromD); break;
+    }
+  }
+#undef UPD
 }
-template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st) {
-  cocg_spmm_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
+template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+  if (fresh) cocg_spmm_kernel<R, true><<<grid_of(a), kThreads, 0, st>>>(a);
+  else cocg_spmm_kernel<R, false><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st) {
+  cocg_residual_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
 }
 
 template void cocg_init<double>(const CocgArgs<double> &, cudaStream_t);
 template void cocg_init<float>(const CocgArgs<float> &, cudaStream_t);
-template void cocg_update<double>(const CocgArgs<double> &, bool, bool, cudaStream_t);
-template void cocg_update<float>(const CocgArgs<float> &, bool, bool, cudaStream_t);
-template void cocg_spmm<double>(const CocgArgs<double> &, cudaStream_t);
-template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t);
+template void cocg_update<double>(const CocgArgs<double> &, bool, int, cudaStream_t);
+template void cocg_update<float>(const CocgArgs<float> &, bool, int, cudaStream_t);
+template void cocg_spmm<double>(const CocgArgs<double> &, cudaStream_t, bool);
+template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t, bool);
+template void cocg_residual<float>(const CocgArgs<float> &, cudaStream_t);
 
 }  // namespace slrf

@@ -13,9 +13,9 @@ struct WScal {
   double r0n2;     // ||r0||^2
   double rn2;      // ||r||^2 after the last update
   int active;      // 1 while the column still iterates
-  int iters;       // updates performed
+  int iters;       // updates performed in the current solve
   int brk;         // breakdown flag
-  int pad;
+  int iters_total; // updates over all refinement steps of the filter apply
 };
 
 constexpr int kThreads = 256;  // threads per COCG block (8 warps)
@@ -57,12 +57,24 @@ struct CocgArgs {
   const double *coefV;  // [k]
   double *U;
   int ldu;
+  // iterative refinement (FP32 path, refine_max >= 2): FP64 correction accumulator
+  // D [n][W] in the scaled units of the first step, the FP64 pattern values and poles
+  // for the FP64 residual, and ||r0||^2 of the first step per w
+  double2 *D64;
+  const double *valA64, *valB64;
+  const double2 *sig64;
+  double *r00;
 };
+
+// Final-update modes: how the last COCG update of a solve delivers its correction.
+enum FinalMode { kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, kFinalUFromD = 4 };
 
 // Launchers (defined in cocg.cu).  All enqueue on `st`.
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);
-template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, bool final_acc, cudaStream_t st);
-template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st);
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int final_mode, cudaStream_t st);
+template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh = false);
+// refinement step s >= 2: r = r0 - (A - sigma B) D (FP64), new COCG scalars per w
+template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st);
 template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : 2; }
 
 // gscale[c] = 1 / max |g[:, c]| (tmp: k words of scratch)

@@ -58,6 +58,8 @@ struct slrf_ctx {
   double *coefV = nullptr;
   double *gscale = nullptr;          // FP32 path: per-column right-hand-side scale
   unsigned long long *gmax = nullptr;
+  double2 *D64 = nullptr;            // FP32 path with refinement: FP64 correction [n][Wmax]
+  double *r00 = nullptr;             // ||r0||^2 of the first refinement step, per w
   int last_k = 0, last_W = 0;
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
   // real n x L blocks (ld = L)
@@ -149,7 +151,7 @@ __global__ void to_float2_kernel(int count, const double2 *a, float2 *b) {
 // out[0] += breakdowns, out[1] += COCG updates of the last filter apply
 __global__ void count_iters_kernel(int W, const WScal *ws, int *out) {
   int c = 0, it = 0;
-  for (int w = threadIdx.x; w < W; w += blockDim.x) { c += ws[w].brk; it += ws[w].iters; }
+  for (int w = threadIdx.x; w < W; w += blockDim.x) { c += ws[w].brk; it += ws[w].iters_total; }
   c = warp_sum(c);
   it = warp_sum(it);
   if ((threadIdx.x & 31) == 0) { atomicAdd(out, c); atomicAdd(out + 1, it); }
@@ -238,64 +240,68 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   ctx->last_k = k;
   ctx->last_W = W;
   const int itm = ctx->o.it_max;
-  ctx->launches += 2 * itm + 1 + (sizeof(R) == 4 ? 3 : 0);
-  auto body = [&](cudaStream_t s) {
-    cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s);
-    if (sizeof(R) == 4) col_scale(ctx->n, k, ctx->G, ctx->L, ctx->gmax, ctx->gscale, s);
-    cocg_init<R>(a, s);
-    for (int it = 1; it <= itm; ++it) {
-      cocg_update<R>(a, it == 1, it == itm, s);
-      if (it < itm) cocg_spmm<R>(a, s);
+  // refinement steps: the FP32 path repeats (FP64 residual, fresh FP32 solve) refine_max times
+  const int nref = (sizeof(R) == 4 && ctx->D64 != nullptr) ? std::max(1, ctx->o.refine_max) : 1;
+  if (nref > 1) {
+    a.D64 = ctx->D64;
+    a.valA64 = ctx->valA;
+    a.valB64 = ctx->valB;
+    a.sig64 = ctx->sig;
+    a.r00 = ctx->r00;
+  }
+  ctx->launches += 2 * itm + 1 + (sizeof(R) == 4 ? 3 : 0) + (int64_t)(nref - 1) * (2 * itm + 1);
+  // one launch sequence for the graph, the direct and the timed path; `kind` tags each
+  // launch for the timing hook (0 other, 1 SpMM, 2 update, 3 init)
+  auto body = [&](cudaStream_t s, auto &&launch) {
+    launch(0, [&] { cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s); });
+    if (sizeof(R) == 4)
+      launch(0, [&] { col_scale(ctx->n, k, ctx->G, ctx->L, ctx->gmax, ctx->gscale, s); });
+    launch(3, [&] { cocg_init<R>(a, s); });
+    for (int step = 1; step <= nref; ++step) {
+      if (step > 1) {
+        launch(0, [&] { cocg_residual<R>(a, s); });
+        launch(1, [&] { cocg_spmm<R>(a, s, true); });
+      }
+      const int fm_last = nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+      for (int it = 1; it <= itm; ++it) {
+        launch(2, [&] { cocg_update<R>(a, it == 1, it == itm ? fm_last : kFinalNone, s); });
+        if (it < itm) launch(1, [&] { cocg_spmm<R>(a, s); });
+      }
     }
   };
+  auto plain = [](int, auto &&fn) { fn(); };
   if (tm != nullptr) {
     // same launches, each bracketed by events on the library stream
-    std::vector<cudaEvent_t> ev(2 * (2 * itm + 1));
-    for (auto &e : ev) CK(cudaEventCreate(&e));
     cudaStream_t s = ctx->st;
-    int e = 0;
-    cocg_prepare(W, k, ctx->m, ctx->mp, ctx->sig, ctx->wt, theta, ctx->cfac, ctx->coefV, ctx->ws, s);
-    if (sizeof(R) == 4) col_scale(ctx->n, k, ctx->G, ctx->L, ctx->gmax, ctx->gscale, s);
-    cudaEventRecord(ev[e++], s);
-    cocg_init<R>(a, s);
-    cudaEventRecord(ev[e++], s);
-    for (int it = 1; it <= itm; ++it) {
-      cudaEventRecord(ev[e++], s);
-      cocg_update<R>(a, it == 1, it == itm, s);
-      cudaEventRecord(ev[e++], s);
-      if (it < itm) {
-        cudaEventRecord(ev[e++], s);
-        cocg_spmm<R>(a, s);
-        cudaEventRecord(ev[e++], s);
-      }
-    }
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
+    auto timed = [&](int kind, auto &&fn) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+      fn();
+      cudaEventRecord(e1, s);
+      evs.push_back({kind, {e0, e1}});
+    };
+    body(s, timed);
     CKL();
     CK(cudaStreamSynchronize(s));
-    float t = 0;
-    e = 0;
-    cudaEventElapsedTime(&t, ev[0], ev[1]);
-    tm->ms_init += t;
-    e = 2;
-    for (int it = 1; it <= itm; ++it) {
-      cudaEventElapsedTime(&t, ev[e], ev[e + 1]);
-      tm->ms_update += t;
-      tm->n_update++;
-      e += 2;
-      if (it < itm) {
-        cudaEventElapsedTime(&t, ev[e], ev[e + 1]);
-        tm->ms_spmm += t;
-        tm->n_spmm++;
-        e += 2;
-      }
+    for (auto &e : evs) {
+      float t = 0;
+      cudaEventElapsedTime(&t, e.second.first, e.second.second);
+      if (e.first == 1) { tm->ms_spmm += t; tm->n_spmm++; }
+      else if (e.first == 2) { tm->ms_update += t; tm->n_update++; }
+      else if (e.first == 3) tm->ms_init += t;
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
     }
-    for (auto &x : ev) cudaEventDestroy(x);
   } else if (capture_ok && ctx->o.use_graph) {
     const int warm = theta != nullptr;
     if (!(ctx->gexec && ctx->g_k == k && ctx->g_warm == warm)) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-      body(ctx->st);
+      body(ctx->st, plain);
       CK(cudaStreamEndCapture(ctx->st, &g));
       cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
       cudaGraphDestroy(g);
@@ -305,7 +311,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
     }
     CK(cudaGraphLaunch(ctx->gexec, ctx->st));
   } else {
-    body(ctx->st);
+    body(ctx->st, plain);
   }
   CKL();
   return SLRF_OK;
@@ -490,7 +496,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   const size_t partial = (size_t)kRowBlocks * ctx->Wmax * kNQ;
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
-  const size_t need = (state + blocks + matrix) + 8 * partial + (64u << 20);
+  const size_t refine = (ctx->mixed && o.refine_max > 1) ? 16 * (size_t)n * ctx->Wmax : 0;
+  const size_t need = (state + blocks + matrix + refine) + 8 * partial + (64u << 20);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(SLRF_ECUDA);
   if (need > fr) return fail(SLRF_ENOMEM);
@@ -577,6 +584,10 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   AL(ctx->coefV, (size_t)L);
   AL(ctx->gscale, (size_t)L);
   AL(ctx->gmax, (size_t)L);
+  if (ctx->mixed && o.refine_max > 1) {
+    AL(ctx->D64, (size_t)n * ctx->Wmax);
+    AL(ctx->r00, ctx->Wmax);
+  }
   // real blocks
   const size_t nb = (size_t)n * L;
   AL(ctx->V, nb); AL(ctx->AV, nb); AL(ctx->BV, nb);

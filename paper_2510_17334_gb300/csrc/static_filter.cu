@@ -180,7 +180,7 @@ extern "C" int slrf_filter_apply_static(const slrf_csr_pair *pc, double gamma, c
   cocg_prepare(W, k, m, mp, sig, wt, theta, cfac, coefV, ws, st);
   cocg_init<double>(ca, st);
   for (int it = 1; it <= o.it_max; ++it) {
-    cocg_update<double>(ca, it == 1, it == o.it_max, st);
+    cocg_update<double>(ca, it == 1, it == o.it_max ? kFinalU : kFinalNone, st);
     if (it < o.it_max) cocg_spmm<double>(ca, st);
   }
   return cudaGetLastError() == cudaSuccess ? SLRF_OK : SLRF_ECUDA;

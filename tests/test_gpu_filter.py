@@ -139,3 +139,30 @@ def test_full_size_sampled_columns(slrf_mod):
     Uo, _ = orc.filter_apply(p.A(), p.B(), V1[:, cols], None, so, wo, it, 1e-10)
     assert rel(U[:, cols], Uo) <= 1e-8
     ctx.close()
+
+
+def test_mixed_refinement_converges_to_the_fp64_filter(slrf_mod):
+    """FP64 iterative refinement around complex-FP32 COCG (refine_max steps): with inner
+    solves long enough to converge, the filter approaches the oracle's exactly-solved FP64
+    filter step by step -- FP32 accuracy after one step, FP64 accuracy after three.  Each
+    FP32 solve stops at 1e-6 of its own right-hand side, about what FP32 can reach.  Both
+    sides use the same pole table (the designed weights differ by ~6e-9 between the two
+    normal-equation solves, which converged solves amplify to ~1e-6 in U)."""
+    p = si.q1_scalar((5, 5, 4), shift=1e-3)
+    lam = sla.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True)
+    gamma = 0.5 * (lam[9] + lam[10])
+    L = 8
+    V1 = si.start_block(p.n, L, 12)
+    so, wo = orc.slrf_poles(8, gamma)
+    Uo, info = orc.filter_apply(p.A(), p.B(), V1, None, so, wo, 2000, 1e-15)
+    errs = []
+    for R in (1, 2, 3):
+        ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L,
+                               slrf_mod.slrf_opts_default(it_max=400, precision=1, refine_max=R, tol_inner=1e-6,
+                                                          poles=so, weights=wo))
+        U = ctx.filter_apply(torch.from_numpy(V1)).cpu().numpy()
+        errs.append(rel(U, Uo))
+        ctx.close()
+    assert errs[0] <= 1e-4
+    assert errs[1] <= 1e-9 and errs[1] < errs[0]
+    assert errs[2] <= 1e-12 and errs[2] <= errs[1]

@@ -211,3 +211,16 @@ def test_solve_q1_41_full_size(slrf_mod):
     assert rs.max() <= 1e-8
     B = wl.pencil.B()
     assert np.abs(X.T @ (B @ X) - np.eye(105)).max() <= 1e-11
+
+
+def test_solve_with_refinement_steps(slrf_mod):
+    """Mixed path with two FP64 refinement steps per filter apply: same eigenpairs."""
+    nodes = (9, 9, 9)
+    p = si.q1_scalar(nodes, shift=1e-3)
+    lam = pins.q1_neumann_eigs(nodes, 1e-3)
+    gamma, cnt = pins.gap_gamma(lam, 25)
+    L = int(np.ceil(1.5 * cnt))
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 5, it_max=20, precision=1, refine_max=2)
+    assert rc == 0 and nf == cnt
+    assert np.all(np.abs(ev - lam[:cnt]) <= np.maximum(1e-8 * lam[:cnt], 1e-9 * lam[0]))
+    assert rs.max() <= 1e-8
