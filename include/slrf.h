@@ -45,7 +45,8 @@ extern "C" {
 #define SLRF_ESTATE (-10)    /* context is in a failed state from an earlier error       */
 
 /* ---- types ---------------------------------------------------------------------- */
-typedef struct slrf_ctx slrf_ctx; /* opaque, owned by the library */
+typedef struct slrf_ctx slrf_ctx;     /* opaque, owned by the library */
+typedef struct slrf_batch slrf_batch; /* opaque: a set of independent problems solved together */
 
 /* A and B on one CSR pattern (all device pointers). */
 typedef struct {
@@ -76,6 +77,7 @@ typedef struct {
   uint64_t seed;          /* seed of the Gaussian start block when V0 is NULL               */
   const double *poles;    /* optional HOST table: m complex poles, (re, im) interleaved     */
   const double *weights;  /* optional HOST table: m complex weights; NULL = SLRF design     */
+  int autotune;           /* 1 = time candidate COCG rows-per-block at setup, keep the fastest */
 } slrf_opts;
 
 /* Statistics of the last slrf_solve (host struct filled by the library). */
@@ -177,6 +179,29 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
 int slrf_solve_host(const slrf_csr_pair *pencil_host, double gamma, int block_L,
                     const slrf_opts *opts, const double *V0, int cap, int *n_found,
                     double *evals, double *X, double *resid, slrf_stats *stats);
+
+/* Batched uneven pencils: P independent problems (each its own pattern, size, gamma and
+ * block width) solved together.  pencils (HOST array of P device pencils), gammas and
+ * blocks (HOST, P entries), opts shared by all (one It_max, precision, ...), stream as
+ * in slrf_setup.  Each problem gets its own context and stream (its real sweeps and
+ * Rayleigh-Ritz steps run concurrently); the COCG phases of all active problems run as
+ * one persistent launch per phase over the work list of (problem, row block, column tile)
+ * items, captured in a CUDA graph.  Errors: as slrf_setup (first failing problem). */
+int slrf_setup_batched(slrf_batch **batch, int P, const slrf_csr_pair *pencils, const double *gammas,
+                       const int *blocks, const slrf_opts *opts, void *stream);
+
+/* Enhanced ParaSLRF (Alg. 2) on every problem of the batch; a problem leaves the batch
+ * when its own stopping rule holds.  V0: HOST array of P device start blocks (n_p x L_p)
+ * or NULL (Gaussian blocks); caps (HOST, P); outputs per problem: n_found[p], status[p]
+ * (HOST), evals[p], X[p] (n_p x caps[p], leading dimension caps[p]), resid[p] (HOST arrays
+ * of P device pointers).  stats (HOST, may be NULL) aggregates all problems; ms_total is
+ * the device time of the whole batch.  Returns SLRF_OK or the first non-OK problem status. */
+int slrf_solve_batched(slrf_batch *batch, const double *const *V0, const int *caps, int *n_found,
+                       double *const *evals, double *const *X, double *const *resid, int *status,
+                       slrf_stats *stats);
+
+/* Release a batch and every context in it.  NULL is accepted. */
+void slrf_destroy_batched(slrf_batch *batch);
 
 /* Eigenvalue adjoint on the pattern (first-order perturbation of a simple eigenvalue
  * of a symmetric-definite pencil, x_i B-normalised):  d lambda_i = x_i^T (dA - lambda_i dB) x_i,

@@ -112,11 +112,10 @@ __device__ bool block_then_grid_reduce(double (&acc)[VEC][NQ], const int W, cons
 // ------------------------------------------------------------------------------ init
 // r0 = c g, p0 = r0, q0 = c (A g - sigma B g); reduce mu0 = p0^T q0, rho0 = r0^T r0, ||r0||^2.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R> a) {
+__device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rb = blockIdx.x, tile = blockIdx.y;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
   C sg[VEC], cf[VEC];
@@ -199,12 +198,11 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R
 // d += alpha p (d = alpha p on the first step); r -= alpha q; reduce rho' and ||r||^2.
 // With final_acc, also U[i][c] = coefV[c] V[i][c] + sum_j 2 Re(w_j d_j).
 template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs<R> a) {
+__device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr bool FINAL = FM != kFinalNone;
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rb = blockIdx.x, tile = blockIdx.y;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
   C al[VEC];
@@ -330,11 +328,10 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs
 // ------------------------------------------------------------------------------ spmm
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
 template <typename R, bool FRESH>
-__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R> a) {
+__device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rb = blockIdx.x, tile = blockIdx.y;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
   C sg[VEC], be[VEC];
@@ -437,11 +434,10 @@ __global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R
 // scalars rho = R^T R, ||R||^2 per w.  Every column with a nonzero residual (and no
 // earlier breakdown) is refined; its FP32 solve stops at tol ||R|| or It_max.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
+__device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rb = blockIdx.x, tile = blockIdx.y;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
   double2 sg[VEC], cf[VEC];
@@ -530,6 +526,64 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgAr
     a.ws[w] = s;
   }
 }
+
+// ------------------------------------------------------------------------------ kernels
+// Single problem: blockIdx.x = row block, blockIdx.y = tile.
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R> a) {
+  cocg_init_body<R>(a, blockIdx.x, blockIdx.y);
+}
+template <typename R, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs<R> a) {
+  cocg_update_body<R, FIRST, FM>(a, blockIdx.x, blockIdx.y);
+}
+template <typename R, bool FRESH>
+__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R> a) {
+  cocg_spmm_body<R, FRESH>(a, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
+  cocg_residual_body<R>(a, blockIdx.x, blockIdx.y);
+}
+
+// Many problems in one persistent launch: work item t of the list belongs to problem p
+// with prefix[p] <= t < prefix[p+1]; inside a problem the row block varies fastest and
+// the tile slowest (as in the single-problem grid).  Blocks stride over the items.
+__device__ __forceinline__ int batch_problem(const int *prefix, int P, int item) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+#define SLRF_BATCH_LOOP(BODY)                                               \
+  const int total = prefix[P];                                              \
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {            \
+    const int pb = batch_problem(prefix, P, item);                          \
+    const CocgArgs<R> &a = args[pb];                                        \
+    const int local = item - prefix[pb];                                    \
+    BODY;                                                                   \
+    __syncthreads();                                                        \
+  }
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 4) cocg_init_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_init_body<R>(a, local % a.nrb, local / a.nrb)))
+}
+template <typename R, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, 4) cocg_update_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_update_body<R, FIRST, FM>(a, local % a.nrb, local / a.nrb)))
+}
+template <typename R, bool FRESH>
+__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_spmm_body<R, FRESH>(a, local % a.nrb, local / a.nrb)))
+}
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2) cocg_residual_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_residual_body<R>(a, local % a.nrb, local / a.nrb)))
+}
+#undef SLRF_BATCH_LOOP
 
 // ------------------------------------------------------------------------------ prepare
 __global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
@@ -636,5 +690,54 @@ template void cocg_update<float>(const CocgArgs<float> &, bool, int, cudaStream_
 template void cocg_spmm<double>(const CocgArgs<double> &, cudaStream_t, bool);
 template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t, bool);
 template void cocg_residual<float>(const CocgArgs<float> &, cudaStream_t);
+
+// ------------------------------------------------------------------------------ batched launchers
+static int batch_grid(int total) { return total < 152 * 4 ? total : 152 * 4; }
+
+template <typename R> void cocg_init_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                    cudaStream_t st) {
+  cocg_init_batched<R><<<batch_grid(total), kThreads, 0, st>>>(args, prefix, P);
+}
+template <typename R> void cocg_update_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                      bool first, int fm, cudaStream_t st) {
+  const int g = batch_grid(total);
+#define UPD(F, M) cocg_update_batched<R, F, M><<<g, kThreads, 0, st>>>(args, prefix, P)
+  if (first) {
+    switch (fm) {
+      case kFinalNone: UPD(true, kFinalNone); break;
+      case kFinalU: UPD(true, kFinalU); break;
+      case kFinalStoreD: UPD(true, kFinalStoreD); break;
+      case kFinalAddD: UPD(true, kFinalAddD); break;
+      default: UPD(true, kFinalUFromD); break;
+    }
+  } else {
+    switch (fm) {
+      case kFinalNone: UPD(false, kFinalNone); break;
+      case kFinalU: UPD(false, kFinalU); break;
+      case kFinalStoreD: UPD(false, kFinalStoreD); break;
+      case kFinalAddD: UPD(false, kFinalAddD); break;
+      default: UPD(false, kFinalUFromD); break;
+    }
+  }
+#undef UPD
+}
+template <typename R> void cocg_spmm_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                    bool fresh, cudaStream_t st) {
+  if (fresh) cocg_spmm_batched<R, true><<<batch_grid(total), kThreads, 0, st>>>(args, prefix, P);
+  else cocg_spmm_batched<R, false><<<batch_grid(total), kThreads, 0, st>>>(args, prefix, P);
+}
+template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                        cudaStream_t st) {
+  cocg_residual_batched<R><<<batch_grid(total), kThreads, 0, st>>>(args, prefix, P);
+}
+#define INST(R)                                                                                            \
+  template void cocg_init_batched_launch<R>(const CocgArgs<R> *, const int *, int, int, cudaStream_t);    \
+  template void cocg_update_batched_launch<R>(const CocgArgs<R> *, const int *, int, int, bool, int,      \
+                                              cudaStream_t);                                              \
+  template void cocg_spmm_batched_launch<R>(const CocgArgs<R> *, const int *, int, int, bool, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+template void cocg_residual_batched_launch<float>(const CocgArgs<float> *, const int *, int, int, cudaStream_t);
 
 }  // namespace slrf

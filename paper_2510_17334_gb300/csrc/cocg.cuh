@@ -80,6 +80,17 @@ template <typename R> __host__ __device__ constexpr int cocg_vec() { return size
 // gscale[c] = 1 / max |g[:, c]| (tmp: k words of scratch)
 void col_scale(int64_t n, int k, const double *g, int ld, unsigned long long *tmp, double *gscale, cudaStream_t st);
 
+// Batched launches: one persistent grid over the work items (row block, tile) of P
+// problems; args (device, P entries) and prefix (device, P + 1 item offsets).
+template <typename R> void cocg_init_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                    cudaStream_t st);
+template <typename R> void cocg_update_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                      bool first, int fm, cudaStream_t st);
+template <typename R> void cocg_spmm_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                    bool fresh, cudaStream_t st);
+template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
+                                                        cudaStream_t st);
+
 // prepare per-w factors: warm start c = 1/(sigma_j - theta_c), else 1; coefV = Phi(theta_c)
 void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
                   const double *theta, double2 *cfac, double *coefV, WScal *ws, cudaStream_t st);

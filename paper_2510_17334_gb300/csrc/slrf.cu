@@ -62,6 +62,7 @@ struct slrf_ctx {
   double *r00 = nullptr;             // ||r0||^2 of the first refinement step, per w
   int last_k = 0, last_W = 0;
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
+  int64_t rpb_tuned = 0;             // autotuned COCG rows per block (0 = default)
   // real n x L blocks (ld = L)
   double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
   double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
@@ -208,16 +209,18 @@ struct FilterTiming {
   int n_spmm = 0, n_update = 0;
 };
 
+// COCG arguments of one filter apply of this context (k columns, optional warm start).
 template <typename R>
-static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, double *U, int ldu,
-                    bool capture_ok, FilterTiming *tm) {
+static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int k, double *U, int ldu, int &nref) {
   const int vec = cocg_vec<R>();
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
   // Row blocks per tile: about as many as the GPU holds resident (152 SMs x 4 blocks), so
   // that the blocks in flight at any time all belong to one or two tiles (the tile index
-  // varies slowest) and the gathered rows of those tiles stay in L2.
-  const int64_t rpb = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
+  // varies slowest) and the gathered rows of those tiles stay in L2.  An autotuned row
+  // count (slrf_opts.autotune) replaces the default.
+  int64_t rpb = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
+  if (ctx->rpb_tuned > 0) rpb = std::max<int64_t>(rpb, ctx->rpb_tuned);
   const int nrb = (int)((ctx->n + rpb - 1) / rpb);
   CocgArgs<R> a{};
   a.n = ctx->n;
@@ -237,11 +240,8 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   a.cfac = ctx->cfac; a.wt = ctx->wt;
   a.gscale = sizeof(R) == 4 ? ctx->gscale : nullptr;
   a.V = X; a.ldv = ldx; a.coefV = ctx->coefV; a.U = U; a.ldu = ldu;
-  ctx->last_k = k;
-  ctx->last_W = W;
-  const int itm = ctx->o.it_max;
   // refinement steps: the FP32 path repeats (FP64 residual, fresh FP32 solve) refine_max times
-  const int nref = (sizeof(R) == 4 && ctx->D64 != nullptr) ? std::max(1, ctx->o.refine_max) : 1;
+  nref = (sizeof(R) == 4 && ctx->D64 != nullptr) ? std::max(1, ctx->o.refine_max) : 1;
   if (nref > 1) {
     a.D64 = ctx->D64;
     a.valA64 = ctx->valA;
@@ -249,6 +249,18 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
     a.sig64 = ctx->sig;
     a.r00 = ctx->r00;
   }
+  ctx->last_k = k;
+  ctx->last_W = W;
+  return a;
+}
+
+template <typename R>
+static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, double *U, int ldu,
+                    bool capture_ok, FilterTiming *tm) {
+  int nref = 1;
+  CocgArgs<R> a = build_cocg_args<R>(ctx, X, ldx, k, U, ldu, nref);
+  const int W = a.W;
+  const int itm = ctx->o.it_max;
   ctx->launches += 2 * itm + 1 + (sizeof(R) == 4 ? 3 : 0) + (int64_t)(nref - 1) * (2 * itm + 1);
   // one launch sequence for the graph, the direct and the timed path; `kind` tags each
   // launch for the timing hook (0 other, 1 SpMM, 2 update, 3 init)
@@ -259,7 +271,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
     launch(3, [&] { cocg_init<R>(a, s); });
     for (int step = 1; step <= nref; ++step) {
       if (step > 1) {
-        launch(0, [&] { cocg_residual<R>(a, s); });
+        if constexpr (sizeof(R) == 4) launch(0, [&] { cocg_residual<R>(a, s); });
         launch(1, [&] { cocg_spmm<R>(a, s, true); });
       }
       const int fm_last = nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
@@ -319,8 +331,8 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
 
 // The real FP64 sweep that starts every pole (Proposition (i), Sec. 4):
 //   zero guess:  g = B X;   warm start:  g = A X - theta B X;   then A g and B g.
-static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, const double *AXp,
-                       const double *BXp, double *U, int ldu, bool capture_ok, FilterTiming *tm = nullptr) {
+static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, const double *AXp,
+                       const double *BXp) {
   const cudaStream_t st = ctx->st;
   const int L = ctx->L;
   if (theta == nullptr) {
@@ -341,8 +353,58 @@ static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
   spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->G, L, k, ctx->AG, ctx->BG, L, st);
   ctx->launches += 1;
   CKL();
+  return SLRF_OK;
+}
+
+static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, const double *AXp,
+                       const double *BXp, double *U, int ldu, bool capture_ok, FilterTiming *tm = nullptr) {
+  int rc = filter_prep(ctx, X, ldx, k, theta, AXp, BXp);
+  if (rc != SLRF_OK) return rc;
   if (ctx->mixed) return run_cocg<float>(ctx, X, ldx, k, theta, U, ldu, capture_ok, tm);
   return run_cocg<double>(ctx, X, ldx, k, theta, U, ldu, capture_ok, tm);
+}
+
+// Autotuner: time one fused SpMM launch for each candidate rows-per-block on a Gaussian
+// block of the full width (after the usual initialisation) and keep the fastest.
+template <typename R>
+static int autotune_rows(slrf_ctx *ctx) {
+  const cudaStream_t st = ctx->st;
+  const int L = ctx->L;
+  gaussian_block(ctx->n, L, ctx->o.seed + 7, ctx->V, L, st);
+  int rc = filter_prep(ctx, ctx->V, L, L, nullptr, nullptr, nullptr);
+  if (rc != SLRF_OK) return rc;
+  const int64_t base = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
+  const int64_t cand[] = {base, 32, 64, 128, 256};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int64_t best_r = 0;
+  for (int64_t c : cand) {
+    if (c < base || c > ctx->n) continue;
+    ctx->rpb_tuned = c;
+    int nref = 1;
+    CocgArgs<R> a = build_cocg_args<R>(ctx, ctx->V, L, L, ctx->U, L, nref);
+    cocg_prepare(a.W, L, ctx->m, ctx->mp, ctx->sig, ctx->wt, nullptr, ctx->cfac, ctx->coefV, ctx->ws, st);
+    if (sizeof(R) == 4) col_scale(ctx->n, L, ctx->G, L, ctx->gmax, ctx->gscale, st);
+    cocg_init<R>(a, st);
+    float t = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      cocg_spmm<R>(a, st);
+      cudaEventRecord(e1, st);
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (t < best) { best = t; best_r = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->rpb_tuned = best_r;
+  CKL();
+  return SLRF_OK;
 }
 
 // ----------------------------------------------------------------------------- RR step
@@ -387,6 +449,107 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
   ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
   CKL();
+  return SLRF_OK;
+}
+
+
+// ----------------------------------------------------------------------------- batched
+struct slrf_batch {
+  int P = 0;
+  std::vector<slrf_ctx *> c;
+  cudaStream_t st = nullptr, ust = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_b = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  std::vector<cudaEvent_t> ev_p;
+  bool mixed = false;
+  void *dargs = nullptr, *hargs = nullptr;
+  int *dprefix = nullptr, *hprefix = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_P = -1, g_total = -1;
+};
+
+static void batch_free(slrf_batch *b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (auto *c : b->c) slrf_destroy(c);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (auto e : b->ev_p) if (e) cudaEventDestroy(e);
+  for (auto e : {b->ev_in, b->ev_b, b->ev_t0, b->ev_t1}) if (e) cudaEventDestroy(e);
+  if (b->dargs) cudaFree(b->dargs);
+  if (b->dprefix) cudaFree(b->dprefix);
+  if (b->hargs) cudaFreeHost(b->hargs);
+  if (b->hprefix) cudaFreeHost(b->hprefix);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+// One persistent batched COCG pass over the active problems (args/prefix already on the
+// device): init, then refine_max x (It_max updates and SpMMs), on the batch stream.
+template <typename R>
+static void batch_cocg(slrf_batch *b, int P, int total, int nref, int itm, cudaStream_t s) {
+  const CocgArgs<R> *args = reinterpret_cast<const CocgArgs<R> *>(b->dargs);
+  const int *pre = b->dprefix;
+  cocg_init_batched_launch<R>(args, pre, P, total, s);
+  for (int step = 1; step <= nref; ++step) {
+    if (step > 1) {
+      if constexpr (sizeof(R) == 4) cocg_residual_batched_launch<R>(args, pre, P, total, s);
+      cocg_spmm_batched_launch<R>(args, pre, P, total, true, s);
+    }
+    const int fm_last = nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+    for (int it = 1; it <= itm; ++it) {
+      cocg_update_batched_launch<R>(args, pre, P, total, it == 1, it == itm ? fm_last : kFinalNone, s);
+      if (it < itm) cocg_spmm_batched_launch<R>(args, pre, P, total, false, s);
+    }
+  }
+}
+
+template <typename R>
+static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const std::vector<int> &kk,
+                              const std::vector<char> &warm, int64_t &launches) {
+  slrf_ctx *ctx = nullptr;  // for CK
+  const int vec = cocg_vec<R>();
+  CocgArgs<R> *ha = reinterpret_cast<CocgArgs<R> *>(b->hargs);
+  int nref = 1, total = 0;
+  const int P = (int)act.size();
+  b->hprefix[0] = 0;
+  for (int i = 0; i < P; ++i) {
+    slrf_ctx *c = b->c[act[i]];
+    const int k = kk[act[i]];
+    const double *th = warm[act[i]] ? c->theta_act : nullptr;
+    int rc = filter_prep(c, c->V, c->L, k, th, warm[act[i]] ? c->AV : nullptr, warm[act[i]] ? c->BV : nullptr);
+    if (rc != SLRF_OK) return rc;
+    ha[i] = build_cocg_args<R>(c, c->V, c->L, k, c->U, c->L, nref);
+    cocg_prepare(ha[i].W, k, c->m, c->mp, c->sig, c->wt, th, c->cfac, c->coefV, c->ws, c->st);
+    if (sizeof(R) == 4) col_scale(c->n, k, c->G, c->L, c->gmax, c->gscale, c->st);
+    launches += 1 + (sizeof(R) == 4 ? 2 : 0);
+    total += ha[i].nrb * (ha[i].W / (32 * vec));
+    b->hprefix[i + 1] = total;
+    CK(cudaEventRecord(b->ev_p[act[i]], c->st));
+    CK(cudaStreamWaitEvent(b->st, b->ev_p[act[i]], 0));
+  }
+  const int itm = b->c[act[0]]->o.it_max;
+  CK(cudaMemcpyAsync(b->dargs, b->hargs, P * sizeof(CocgArgs<R>), cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(b->dprefix, b->hprefix, (P + 1) * sizeof(int), cudaMemcpyHostToDevice, b->st));
+  launches += 1 + (int64_t)nref * (2 * itm - 1) + (nref - 1) * (sizeof(R) == 4 ? 2 : 1);
+  if (b->c[act[0]]->o.use_graph) {
+    if (!(b->gexec && b->g_P == P && b->g_total == total)) {
+      if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+      batch_cocg<R>(b, P, total, nref, itm, b->st);
+      CK(cudaStreamEndCapture(b->st, &g));
+      cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return SLRF_ECUDA;
+      b->g_P = P;
+      b->g_total = total;
+    }
+    CK(cudaGraphLaunch(b->gexec, b->st));
+  } else {
+    batch_cocg<R>(b, P, total, nref, itm, b->st);
+  }
+  if (cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
+  CK(cudaEventRecord(b->ev_b, b->st));
+  for (int i = 0; i < P; ++i) CK(cudaStreamWaitEvent(b->c[act[i]]->st, b->ev_b, 0));
   return SLRF_OK;
 }
 
@@ -615,6 +778,10 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
 #undef AL
   for (auto &e : ctx->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(SLRF_ECUDA);
+  if (o.autotune) {
+    const int arc = ctx->mixed ? autotune_rows<float>(ctx) : autotune_rows<double>(ctx);
+    if (arc != SLRF_OK) return fail(arc);
+  }
   if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(SLRF_ECUDA);
   *out = ctx;
   return SLRF_OK;
@@ -883,6 +1050,148 @@ int slrf_solve_host(const slrf_csr_pair *ph, double gamma, int block_L, const sl
   cudaFree(buf);
   cudaStreamDestroy(st);
   return rc;
+}
+
+int slrf_setup_batched(slrf_batch **out, int P, const slrf_csr_pair *pencils, const double *gammas, const int *blocks,
+                       const slrf_opts *opts, void *stream) {
+  if (!out) return SLRF_EINVAL;
+  *out = nullptr;
+  if (P < 1 || !pencils || !gammas || !blocks) return SLRF_EINVAL;
+  slrf_batch *b = new (std::nothrow) slrf_batch();
+  if (!b) return SLRF_ENOMEM;
+  b->P = P;
+  b->ust = (cudaStream_t)stream;
+  b->c.assign(P, nullptr);
+  b->ev_p.assign(P, nullptr);
+  for (int p = 0; p < P; ++p) {
+    const int rc = slrf_setup(&b->c[p], &pencils[p], gammas[p], blocks[p], opts, stream);
+    if (rc != SLRF_OK) {
+      batch_free(b);
+      return rc;
+    }
+  }
+  b->mixed = b->c[0]->mixed;
+  const size_t asz = std::max(sizeof(CocgArgs<double>), sizeof(CocgArgs<float>));
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->ev_t0) != cudaSuccess || cudaEventCreate(&b->ev_t1) != cudaSuccess ||
+      cudaMalloc(&b->dargs, P * asz) != cudaSuccess || cudaMalloc(&b->dprefix, (P + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&b->hargs, P * asz) != cudaSuccess || cudaMallocHost(&b->hprefix, (P + 1) * sizeof(int)) != cudaSuccess) {
+    batch_free(b);
+    return SLRF_ECUDA;
+  }
+  for (int p = 0; p < P; ++p)
+    if (cudaEventCreateWithFlags(&b->ev_p[p], cudaEventDisableTiming) != cudaSuccess) {
+      batch_free(b);
+      return SLRF_ECUDA;
+    }
+  *out = b;
+  return SLRF_OK;
+}
+
+void slrf_destroy_batched(slrf_batch *b) { batch_free(b); }
+
+int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, int *n_found, double *const *evals,
+                       double *const *Xo, double *const *resid, int *status, slrf_stats *stats) {
+  if (!b || !caps || !n_found || !status) return SLRF_EINVAL;
+  const int P = b->P;
+  for (int p = 0; p < P; ++p) {
+    if (b->c[p]->status != SLRF_OK) return SLRF_ESTATE;
+    if (caps[p] < 0 || (caps[p] > 0 && (!evals || !Xo || !resid || !evals[p] || !Xo[p] || !resid[p]))) return SLRF_EINVAL;
+  }
+  slrf_ctx *ctx = nullptr;  // for CK
+  // fork: every problem stream and the batch stream start after the caller's stream
+  CK(cudaEventRecord(b->ev_in, b->ust));
+  CK(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+  for (auto *c : b->c) CK(cudaStreamWaitEvent(c->st, b->ev_in, 0));
+  CK(cudaEventRecord(b->ev_t0, b->st));
+  std::vector<int> kk(P), nconv(P, 0), quiet(P, 0), outer_of(P, 0);
+  std::vector<char> done(P, 0), warm(P, 0);
+  std::vector<int> st_p(P, SLRF_ENOCONV);
+  int64_t launches = 0;
+  slrf_stats S{};
+  for (int p = 0; p < P; ++p) {
+    slrf_ctx *c = b->c[p];
+    c->launches = 0;
+    kk[p] = c->L;
+    if (V0 && V0[p]) copy_block(c->n, c->L, V0[p], c->L, c->V, c->L, c->st);
+    else gaussian_block(c->n, c->L, c->o.seed + p, c->V, c->L, c->st);
+    CK(cudaMemsetAsync(c->iflags, 0, 16 * sizeof(int), c->st));
+    launches += 1;
+  }
+  const int outer_max = b->c[0]->o.outer_max;
+  int outer = 0;
+  for (outer = 1; outer <= outer_max; ++outer) {
+    std::vector<int> act;
+    for (int p = 0; p < P; ++p)
+      if (!done[p]) act.push_back(p);
+    if (act.empty()) break;
+    const int rc = b->mixed ? batch_outer_filter<float>(b, act, kk, warm, launches)
+                            : batch_outer_filter<double>(b, act, kk, warm, launches);
+    if (rc != SLRF_OK) return rc;
+    for (int p : act) {
+      slrf_ctx *c = b->c[p];
+      const int k = kk[p];
+      count_iters_kernel<<<1, 256, 0, c->st>>>(c->last_W, c->ws, c->iflags + 6);
+      S.column_solves += (int64_t)c->m * k;
+      int r2 = rr_impl(c, c->U, k, c->X, c->BX, c->o.lock ? nconv[p] : 0, c->L);
+      if (r2 != SLRF_OK) return r2;
+      lock_decide(k, c->theta, c->res, c->gamma, c->o.tol_eig, c->o.lock, c->L, c->iflags, c->dst_x, c->dst_v,
+                  c->Theta, c->Res, c->theta_act, c->st);
+      lock_gather(c->n, k, c->Vt, c->AVt, c->BVt, c->L, c->sgn, c->dst_x, c->dst_v, c->X, c->BX, c->L, c->V, c->AV,
+                  c->BV, c->L, c->st);
+      CK(cudaMemcpyAsync(c->h_iflags, c->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      launches += 3;
+    }
+    for (int p : act) {
+      slrf_ctx *c = b->c[p];
+      CK(cudaStreamSynchronize(c->st));
+      const int *hf = c->h_iflags;
+      outer_of[p] = outer;
+      if (hf[9] != 0) { st_p[p] = SLRF_ETIMEOUT; done[p] = 1; continue; }
+      if (hf[4] != 0) { st_p[p] = SLRF_ECHOL; done[p] = 1; continue; }
+      nconv[p] = hf[0];
+      kk[p] = hf[1];
+      warm[p] = c->o.warm_start ? 1 : 0;
+      if (kk[p] < 1) { st_p[p] = SLRF_OK; done[p] = 1; continue; }
+      quiet[p] = hf[2] ? 0 : quiet[p] + 1;
+      if (quiet[p] >= 2 && (c->o.nev <= 0 || nconv[p] >= c->o.nev)) { st_p[p] = SLRF_OK; done[p] = 1; }
+    }
+  }
+  int worst = SLRF_OK;
+  for (int p = 0; p < P; ++p) {
+    slrf_ctx *c = b->c[p];
+    n_found[p] = nconv[p];
+    const int cnt = std::min(nconv[p], caps[p]);
+    if (nconv[p] > 0 && cnt > 0) {
+      final_rank_kernel<<<1, 256, 0, c->st>>>(nconv[p], c->Theta, c->dst_x);
+      const int64_t tot = c->n * nconv[p];
+      final_gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c->st>>>(c->n, nconv[p], cnt, c->dst_x, c->Theta,
+                                                                          c->Res, c->X, c->L, evals[p], Xo[p],
+                                                                          caps[p], resid[p]);
+      launches += 2;
+    }
+    if (st_p[p] == SLRF_OK && nconv[p] > caps[p]) st_p[p] = SLRF_ETRUNC;
+    status[p] = st_p[p];
+    if (st_p[p] != SLRF_OK && worst == SLRF_OK) worst = st_p[p];
+    CK(cudaEventRecord(b->ev_p[p], c->st));
+    CK(cudaStreamWaitEvent(b->st, b->ev_p[p], 0));
+    S.column_iterations += c->h_iflags[7];
+    S.breakdowns += c->h_iflags[6];
+    S.n_conv += nconv[p];
+    launches += c->launches;
+  }
+  CK(cudaEventRecord(b->ev_t1, b->st));
+  CK(cudaStreamWaitEvent(b->ust, b->ev_t1, 0));
+  CK(cudaEventSynchronize(b->ev_t1));
+  float tt = 0;
+  cudaEventElapsedTime(&tt, b->ev_t0, b->ev_t1);
+  S.ms_total = tt;
+  S.outer_iters = outer > outer_max ? outer_max : outer - 1;
+  S.kernel_launches = launches;
+  if (stats) *stats = S;
+  return worst;
 }
 
 int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, int ldx, const double *g_eval,

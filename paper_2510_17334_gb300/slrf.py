@@ -31,7 +31,8 @@ SLRF_ESTATE = -10
 SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_apply", "slrf_filter_timing",
            "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
-           "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static")
+           "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static", "slrf_setup_batched",
+           "slrf_solve_batched", "slrf_destroy_batched")
 
 
 class SlrfError(RuntimeError):
@@ -50,7 +51,7 @@ class Opts(ct.Structure):
                 ("it_max", ct.c_int), ("refine_max", ct.c_int), ("outer_max", ct.c_int),
                 ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
                 ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
-                ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p)]
+                ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -84,6 +85,10 @@ def lib() -> ct.CDLL:
         L.slrf_solve_host.argtypes = [ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp, i, ct.POINTER(i), vp, vp, vp,
                                       ct.POINTER(Stats)]
         L.slrf_eig_grad.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp]
+        L.slrf_setup_batched.argtypes = [ct.POINTER(vp), i, ct.POINTER(CsrPair), vp, vp, ct.POINTER(Opts), vp]
+        L.slrf_solve_batched.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ct.POINTER(Stats)]
+        L.slrf_destroy_batched.argtypes = [vp]
+        L.slrf_destroy_batched.restype = None
         L.slrf_filter_apply_static.argtypes = [ct.POINTER(CsrPair), d, ct.POINTER(Opts), vp, i, vp, vp, vp]
         L.slrf_destroy.argtypes = [vp]
         L.slrf_destroy.restype = None
@@ -241,6 +246,71 @@ class Context:
         _check(lib().slrf_eig_grad(self.h, k, _ptr(evals), _ptr(X), k, _ptr(g), _ptr(gX), _ptr(gA), _ptr(gB)),
                "slrf_eig_grad")
         return gA, gB
+
+
+class Batch:
+    """Owns one ``slrf_batch`` (slrf_setup_batched ... slrf_destroy_batched): independent
+    problems whose COCG phases run in one persistent launch."""
+
+    def __init__(self, problems, gammas, blocks, opts: Opts | None = None, stream=None):
+        """problems: list of (rowptr, col, valA, valB) host or device arrays."""
+        self.P = len(problems)
+        self.opts = opts if opts is not None else slrf_opts_default()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.mats = []
+        pairs = (CsrPair * self.P)()
+        for i, (rp, c, a, b) in enumerate(problems):
+            m = (_dev(torch.as_tensor(rp), torch.int64), _dev(torch.as_tensor(c), torch.int32),
+                 _dev(torch.as_tensor(a), torch.float64), _dev(torch.as_tensor(b), torch.float64))
+            self.mats.append(m)
+            pairs[i] = CsrPair(int(m[0].numel() - 1), int(m[1].numel()), _ptr(m[0]), _ptr(m[1]), _ptr(m[2]),
+                               _ptr(m[3]))
+        self.n = [int(m[0].numel() - 1) for m in self.mats]
+        self.blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        h = ct.c_void_p()
+        _check(lib().slrf_setup_batched(ct.byref(h), self.P, pairs, _ptr(g), _ptr(self.blocks), ct.byref(self.opts),
+                                        ct.c_void_p(self.stream.cuda_stream)), "slrf_setup_batched")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().slrf_destroy_batched(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, V0=None, caps=None, check=True):
+        caps = np.ascontiguousarray(self.blocks if caps is None else caps, dtype=np.int32)
+        v0 = None
+        keep = []
+        if V0 is not None:
+            v0 = (ct.c_void_p * self.P)()
+            for i, v in enumerate(V0):
+                t = _dev(torch.as_tensor(v), torch.float64)
+                keep.append(t)
+                v0[i] = t.data_ptr()
+        ev = [torch.zeros(max(int(c), 1), dtype=torch.float64, device="cuda") for c in caps]
+        X = [torch.zeros((n, max(int(c), 1)), dtype=torch.float64, device="cuda") for n, c in zip(self.n, caps)]
+        rs = [torch.zeros(max(int(c), 1), dtype=torch.float64, device="cuda") for c in caps]
+        pe = (ct.c_void_p * self.P)(*[t.data_ptr() for t in ev])
+        px = (ct.c_void_p * self.P)(*[t.data_ptr() for t in X])
+        pr = (ct.c_void_p * self.P)(*[t.data_ptr() for t in rs])
+        nf = np.zeros(self.P, dtype=np.int32)
+        stt = np.zeros(self.P, dtype=np.int32)
+        st = Stats()
+        rc = lib().slrf_solve_batched(self.h, v0, _ptr(caps), _ptr(nf), pe, px, pr, _ptr(stt), ct.byref(st))
+        if check:
+            _check(rc, "slrf_solve_batched")
+        out = []
+        for i in range(self.P):
+            c = min(int(nf[i]), int(caps[i]))
+            out.append((int(stt[i]), int(nf[i]), ev[i][:c], X[i][:, :c], rs[i][:c]))
+        return rc, out, st.as_dict()
 
 
 def filter_apply_static(rowptr, col, valA, valB, gamma, opts, X, theta=None, U=None, stream=None):
