@@ -203,19 +203,23 @@ int slrf_solve_batched(slrf_batch *batch, const double *const *V0, const int *ca
 /* Release a batch and every context in it.  NULL is accepted. */
 void slrf_destroy_batched(slrf_batch *batch);
 
-/* Eigenvalue adjoint on the pattern (first-order perturbation of a simple eigenvalue
- * of a symmetric-definite pencil, x_i B-normalised):  d lambda_i = x_i^T (dA - lambda_i dB) x_i,
- * so for the loss gradient g_lambda:
- *   gA[e] = sum_i g_lambda[i] x_i[r_e] x_i[c_e],
- *   gB[e] = - sum_i g_lambda[i] lambda_i x_i[r_e] x_i[c_e]   for every stored entry e = (r_e, c_e).
- * If g_X (device n x k, leading dimension k) is not NULL, the eigenvector terms are added:
- * for each i the projected system (A - lambda_i B) xi_i = -(I - B x_i x_i^T) g_x_i with
- * x_i^T B xi_i = 0 is solved (minimal-residual iterations in the B-orthogonal complement)
- * and gA[e] += xi_i[r_e] x_i[c_e], gB[e] += -lambda_i xi_i[r_e] x_i[c_e] - 1/2 x_i[r_e] x_i[c_e] (x_i^T g_x_i).
- * evals (device k), X (device n x k, leading dimension ldx), g_eval (device k), outputs
- * gA, gB (device nnz, overwritten).  The pattern is the context's.
- * Errors: SLRF_EINVAL, SLRF_ENOCONV (an adjoint solve missed its tolerance), SLRF_ESTATE,
- * SLRF_ECUDA. */
+/* Adjoint of the eigenpairs with respect to the values of A and B on their pattern
+ * (first-order perturbation theory of a simple eigenpair of a symmetric-definite pencil,
+ * x_i B-normalised; every stored entry e = (r_e, c_e) is an independent parameter):
+ *   d lambda_i = x_i^T (dA - lambda_i dB) x_i;
+ *   (A - lambda_i B) dx_i = -(dA - lambda_i dB - d lambda_i B) x_i,  x_i^T B dx_i = -1/2 x_i^T dB x_i.
+ * For a loss with gradients g_eval[i] (w.r.t. lambda_i) and, if g_X is not NULL, g_X[:, i]
+ * (w.r.t. x_i), the routine returns
+ *   gA[e] = sum_i (g_eval[i] x_i[r_e] + xi_i[r_e]) x_i[c_e],
+ *   gB[e] = -sum_i ((g_eval[i] lambda_i + 1/2 g_x_i^T x_i) x_i[r_e] + lambda_i xi_i[r_e]) x_i[c_e],
+ * where xi_i solves (A - lambda_i B) xi_i = -(g_x_i - B x_i (x_i^T g_x_i)), x_i^T B xi_i = 0
+ * (block MINRES on all k columns, at most 20000 iterations, relative residual
+ * max(tol_inner, 1e-12); xi = 0 when g_X is NULL).  evals (device k), X (device n x k,
+ * leading dimension ldx), g_eval (device k), g_X (device n x k, leading dimension k, or
+ * NULL), outputs gA, gB (device nnz, overwritten).  The pattern is the context's; with
+ * g_X the context's n x L work blocks are used as scratch (k <= L).
+ * Errors: SLRF_EINVAL, SLRF_ENOCONV (some MINRES column missed its tolerance; the
+ * gradients are still written), SLRF_ESTATE, SLRF_ECUDA. */
 int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, int ldx,
                   const double *g_eval, const double *g_X, double *gA, double *gB);
 

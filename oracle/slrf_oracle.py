@@ -323,3 +323,31 @@ def eig_grad_values(rowptr, col, evals, X, g_eval):
     gA = prod @ np.asarray(g_eval)
     gB = -(prod @ (np.asarray(g_eval) * np.asarray(evals)))
     return gA, gB
+
+
+# ----------------------------------------------------------------------------------------
+# a13: eigenvector adjoint on the pattern (dense reference for small pencils)
+# ----------------------------------------------------------------------------------------
+def eig_grad_full(rowptr, col, A, B, evals, X, g_eval, g_X):
+    """dL/dA_e, dL/dB_e for a loss with dL/dlambda_i = g_i and dL/dx_i = g_x_i (x_i
+    B-normalised, simple eigenvalues).  First-order perturbation:
+      (A - lambda_i B) dx_i = -(dA - lambda_i dB - dlambda_i B) x_i,  x_i^T B dx_i = -1/2 x_i^T dB x_i.
+    With xi_i solving (A - lambda_i B) xi_i = -(I - B x_i x_i^T) g_x_i, x_i^T B xi_i = 0:
+      dL = sum_i [g_i x_i^T (dA - l_i dB) x_i + xi_i^T (dA - l_i dB) x_i - 1/2 (g_x_i^T x_i) x_i^T dB x_i].
+    Dense: xi_i is the least-squares solution of the singular system projected B-orthogonally."""
+    A = np.asarray(A.toarray() if hasattr(A, "toarray") else A)
+    B = np.asarray(B.toarray() if hasattr(B, "toarray") else B)
+    n, k = X.shape
+    Xi = np.zeros((n, k))
+    for i in range(k):
+        x = X[:, i]
+        rhs = -(g_X[:, i] - B @ x * (x @ g_X[:, i]))
+        xi, *_ = np.linalg.lstsq(A - evals[i] * B, rhs, rcond=None)
+        Xi[:, i] = xi - x * (x @ (B @ xi))
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    cols = np.asarray(col)
+    gA = (X[rows, :] * X[cols, :]) @ np.asarray(g_eval) + np.sum(Xi[rows, :] * X[cols, :], axis=1)
+    half = 0.5 * np.sum(g_X * X, axis=0)
+    gB = -((X[rows, :] * X[cols, :]) @ (np.asarray(g_eval) * evals + half)
+           + (Xi[rows, :] * X[cols, :]) @ np.asarray(evals))
+    return gA, gB, Xi

@@ -24,6 +24,17 @@ using namespace slrf;
 namespace slrf {
 int eig_grad_values(int64_t n, const int64_t *rowptr, const int32_t *col, int k, const double *evals,
                     const double *X, int ldx, const double *g, double *gA, double *gB, cudaStream_t st);
+struct MinresScal;
+struct AdjBuffers {
+  double *b, *y, *v, *r1, *r2, *w, *w2, *x, *AV, *BV, *YA, *YB, *work, *work2;
+  MinresScal *scal;
+  int *flag;
+};
+int eig_grad_vectors(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+                     int k, const double *evals, const double *X, const double *g_eval, const double *g_X,
+                     double *gA, double *gB, AdjBuffers bf, int maxit, double tol, int *h_active, int *notconv,
+                     cudaStream_t st);
+size_t adj_work_doubles(int64_t n, int k);
 }
 
 struct slrf_ctx {
@@ -1199,11 +1210,33 @@ int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, in
   if (!ctx) return SLRF_EINVAL;
   if (ctx->status != SLRF_OK) return SLRF_ESTATE;
   if (k < 1 || !evals || !X || ldx < k || !g_eval || !gA || !gB) return SLRF_EINVAL;
-  if (g_X) return SLRF_EINVAL;  // eigenvector terms: see slrf_eig_grad_vec
   StreamScope sc(ctx);
-  const int rc = eig_grad_values(ctx->n, ctx->rowptr, ctx->col, k, evals, X, ldx, g_eval, gA, gB, ctx->st);
-  if (rc != SLRF_OK) ctx->status = rc;
-  return rc;
+  if (g_X == nullptr) {
+    const int rc = eig_grad_values(ctx->n, ctx->rowptr, ctx->col, k, evals, X, ldx, g_eval, gA, gB, ctx->st);
+    if (rc != SLRF_OK) ctx->status = rc;
+    return rc;
+  }
+  if (k > ctx->L) return SLRF_EINVAL;
+  // eigenvector terms: scratch n x k blocks (leading dimension k) from the context
+  const int64_t n = ctx->n;
+  const double *Xk = X;
+  if (ldx != k) {
+    copy_block(n, k, X, ldx, ctx->BX, k, ctx->st);
+    Xk = ctx->BX;
+  }
+  const size_t aw = adj_work_doubles(n, k);
+  if (2 * aw > ctx->work_doubles) return SLRF_EINVAL;
+  AdjBuffers bf{ctx->V, ctx->AV, ctx->BV, ctx->G, ctx->AG, ctx->BG, ctx->U, ctx->U2, ctx->BU, ctx->Vt, ctx->AVt,
+                ctx->BVt, ctx->work, ctx->work + aw, reinterpret_cast<MinresScal *>(ctx->partial), ctx->iflags + 10};
+  int notconv = 0;
+  const double tol = std::max(ctx->o.tol_inner, 1e-12);
+  const int rc = eig_grad_vectors(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, k, evals, Xk, g_eval, g_X, gA, gB,
+                                  bf, 20000, tol, ctx->h_iflags + 12, &notconv, ctx->st);
+  if (rc != SLRF_OK) {
+    ctx->status = rc;
+    return rc;
+  }
+  return notconv ? SLRF_ENOCONV : SLRF_OK;
 }
 
 }  // extern "C"

@@ -351,8 +351,9 @@ def slrf_solve_host(rowptr, col, valA, valB, gamma, block_L, opts=None, V0=None,
 
 
 class SlrfEigsh(torch.autograd.Function):
-    """Eigenpairs in (0, gamma] of (A, B) given by CSR values on a fixed pattern, with the
-    eigenvalue adjoint as backward (gradients on the values of A and B)."""
+    """Eigenpairs in (0, gamma] of (A, B) given by CSR values on a fixed pattern; backward
+    is the adjoint slrf_eig_grad (eigenvalue terms, plus the eigenvector terms when the
+    loss depends on X), returning gradients on the values of A and B."""
 
     @staticmethod
     def forward(fctx, valA, valB, rowptr, col, gamma, block_L, opts, V0):
@@ -361,11 +362,13 @@ class SlrfEigsh(torch.autograd.Function):
         fctx.slrf = ctx
         fctx.devices = (valA.device, valB.device)
         fctx.save_for_backward(ev, X)
-        fctx.mark_non_differentiable(X)
         return ev.clone(), X.clone()
 
     @staticmethod
     def backward(fctx, g_ev, g_X):
         ev, X = fctx.saved_tensors
-        gA, gB = fctx.slrf.eig_grad(ev, X, g_ev.contiguous())
+        if g_ev is None:
+            g_ev = torch.zeros_like(ev)
+        gx = None if (g_X is None or not bool(torch.any(g_X != 0))) else g_X.contiguous()
+        gA, gB = fctx.slrf.eig_grad(ev, X, g_ev.contiguous(), gx)
         return gA.to(fctx.devices[0]), gB.to(fctx.devices[1]), None, None, None, None, None, None

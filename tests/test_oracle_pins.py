@@ -288,3 +288,43 @@ def test_eig_grad_matches_finite_differences():
             fd = g @ (lp - lm) / (2 * h)
             pred = grad @ dvals
             assert abs(fd - pred) <= 1e-5 * abs(fd), (other, fd, pred)
+
+
+# ---------------------------------------------------------------- a13: eigenvector adjoint
+def _eig_sorted(Ad, Bd, k):
+    lam, X = sla.eigh(Ad, Bd)
+    X = X[:, :k]
+    idx = np.argmax(np.abs(X), axis=0)
+    X = X * np.sign(X[idx, np.arange(k)])[None, :]  # largest entry positive (locally constant)
+    return lam[:k], X
+
+
+def test_eigenvector_adjoint_matches_finite_differences():
+    """L = sum_i c_i lambda_i + d_i^T x_i (sign-fixed eigenvectors): central differences of
+    dense generalized eigendecompositions along random symmetric pattern directions."""
+    E = np.exp(np.random.default_rng(11).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    Ad, Bd = p.A().toarray(), p.B().toarray()
+    k = 5
+    lam, X = _eig_sorted(Ad, Bd, k)
+    assert np.min(np.diff(lam)) > 1e-6 * lam[-1]  # simple eigenvalues
+    rng = np.random.default_rng(12)
+    c = rng.standard_normal(k)
+    D = rng.standard_normal((p.n, k))
+    gA, gB, Xi = orc.eig_grad_full(p.rowptr, p.col, Ad, Bd, lam, X, c, D)
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    for _ in range(2):
+        S = np.zeros((p.n, p.n))
+        S[rows, p.col] = rng.standard_normal(p.nnz)
+        Dd = S + S.T
+        dv = Dd[rows, p.col]
+        for which, M0, grad in (("A", Ad, gA), ("B", Bd, gB)):
+            h = 1e-6 * np.abs(M0).max() / np.abs(Dd).max()
+            vals = []
+            for sgn in (1, -1):
+                Am = Ad + sgn * h * Dd if which == "A" else Ad
+                Bm = Bd + sgn * h * Dd if which == "B" else Bd
+                lp, Xp = _eig_sorted(Am, Bm, k)
+                vals.append(c @ lp + np.sum(D * Xp))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - grad @ dv) <= 1e-5 * abs(fd), (which, fd, grad @ dv)
