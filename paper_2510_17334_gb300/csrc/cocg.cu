@@ -27,16 +27,19 @@ namespace slrf {
 
 template <typename R> struct Vec;
 template <> struct Vec<double> { double2 z[1]; };
-template <> struct Vec<float> { float2 z[2]; };
+template <> struct Vec<float> { float2 z[SLRF_F32_VEC]; };
 
 template <typename R> __device__ __forceinline__ Vec<R> ldv(const cx_t<R> *p) {
   Vec<R> v;
   if constexpr (sizeof(R) == 8) {
     v.z[0] = *reinterpret_cast<const double2 *>(p);
   } else {
-    float4 t = *reinterpret_cast<const float4 *>(p);
-    v.z[0] = make_float2(t.x, t.y);
-    v.z[1] = make_float2(t.z, t.w);
+#pragma unroll
+    for (int j = 0; j < SLRF_F32_VEC / 2; ++j) {
+      const float4 t = reinterpret_cast<const float4 *>(p)[j];
+      v.z[2 * j] = make_float2(t.x, t.y);
+      v.z[2 * j + 1] = make_float2(t.z, t.w);
+    }
   }
   return v;
 }
@@ -44,7 +47,9 @@ template <typename R> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<
   if constexpr (sizeof(R) == 8) {
     *reinterpret_cast<double2 *>(p) = v.z[0];
   } else {
-    *reinterpret_cast<float4 *>(p) = make_float4(v.z[0].x, v.z[0].y, v.z[1].x, v.z[1].y);
+#pragma unroll
+    for (int j = 0; j < SLRF_F32_VEC / 2; ++j)
+      reinterpret_cast<float4 *>(p)[j] = make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y);
   }
 }
 
@@ -530,15 +535,15 @@ __device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const i
 // ------------------------------------------------------------------------------ kernels
 // Single problem: blockIdx.x = row block, blockIdx.y = tile.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 4) cocg_init_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_init_kernel(const CocgArgs<R> a) {
   cocg_init_body<R>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, 4) cocg_update_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(const CocgArgs<R> a) {
   cocg_update_body<R, FIRST, FM>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R, bool FRESH>
-__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_kernel(const CocgArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_kernel(const CocgArgs<R> a) {
   cocg_spmm_body<R, FRESH>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R>
@@ -568,15 +573,15 @@ __device__ __forceinline__ int batch_problem(const int *prefix, int P, int item)
     __syncthreads();                                                        \
   }
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 4) cocg_init_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_init_batched(const CocgArgs<R> *args, const int *prefix, int P) {
   SLRF_BATCH_LOOP((cocg_init_body<R>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, 4) cocg_update_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_batched(const CocgArgs<R> *args, const int *prefix, int P) {
   SLRF_BATCH_LOOP((cocg_update_body<R, FIRST, FM>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R, bool FRESH>
-__global__ void __launch_bounds__(kThreads, 4) cocg_spmm_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_batched(const CocgArgs<R> *args, const int *prefix, int P) {
   SLRF_BATCH_LOOP((cocg_spmm_body<R, FRESH>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R>

@@ -75,7 +75,16 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fin
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh = false);
 // refinement step s >= 2: r = r0 - (A - sigma B) D (FP64), new COCG scalars per w
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st);
-template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : 2; }
+// complex entries per lane: one 16-byte value in FP64, SLRF_F32_VEC (two 16-byte loads) in FP32
+#ifndef SLRF_F32_VEC
+#define SLRF_F32_VEC 2
+#endif
+template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : SLRF_F32_VEC; }
+// resident blocks per SM the COCG kernels are compiled for (sets their register budget)
+#ifndef SLRF_F32_MINB
+#define SLRF_F32_MINB 4
+#endif
+template <typename R> __host__ __device__ constexpr int cocg_minb() { return sizeof(R) == 8 ? 4 : SLRF_F32_MINB; }
 
 // gscale[c] = 1 / max |g[:, c]| (tmp: k words of scratch)
 void col_scale(int64_t n, int k, const double *g, int ld, unsigned long long *tmp, double *gscale, cudaStream_t st);

@@ -116,7 +116,8 @@ constexpr int kGR = 16;
 __global__ void __launch_bounds__(256) gram_partial_kernel(int64_t n, const double *__restrict__ X, int ldx, int k1,
                                                            const double *__restrict__ Y, int ldy, int k2,
                                                            int64_t rows_per_chunk, bool sym,
-                                                           double *__restrict__ work) {
+                                                           double *__restrict__ work, const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   const int ti = blockIdx.x, tj = blockIdx.y, z = blockIdx.z;
   if (sym && ti > tj) return;
   __shared__ double xs[kGR][kGT];
@@ -156,7 +157,56 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(int64_t n, const doub
     }
 }
 
-__global__ void gram_reduce_kernel(int k1, int k2, int nz, bool sym, const double *work, double *C, int ldc) {
+// The same product with FP32 inputs and FP32 accumulation inside each row chunk (chunk
+// partials are summed in FP64): a Gram accurate to ~1e-6 relative, used where a later
+// FP64 pass removes its error (first Cholesky-QR pass, first CGS pass).
+__global__ void __launch_bounds__(256) gram32_partial_kernel(int64_t n, const double *__restrict__ X, int ldx, int k1,
+                                                             const double *__restrict__ Y, int ldy, int k2,
+                                                             int64_t rows_per_chunk, bool sym,
+                                                             double *__restrict__ work, const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
+  const int ti = blockIdx.x, tj = blockIdx.y, z = blockIdx.z;
+  if (sym && ti > tj) return;
+  __shared__ float xs[kGR][kGT];
+  __shared__ float ys[kGR][kGT];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  const int64_t r0 = (int64_t)z * rows_per_chunk;
+  const int64_t r1 = (r0 + rows_per_chunk < n) ? r0 + rows_per_chunk : n;
+  for (int64_t rr = r0; rr < r1; rr += kGR) {
+    for (int t = threadIdx.x; t < kGR * kGT; t += 256) {
+      const int lr = t / kGT, lc = t % kGT;
+      const int64_t row = rr + lr;
+      const int cx = ti * kGT + lc, cy = tj * kGT + lc;
+      xs[lr][lc] = (row < r1 && cx < k1) ? (float)X[row * ldx + cx] : 0.0f;
+      ys[lr][lc] = (row < r1 && cy < k2) ? (float)Y[row * ldy + cy] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int lr = 0; lr < kGR; ++lr) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = xs[lr][ty * 4 + u]; b[u] = ys[lr][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double *out = work + (size_t)z * k1 * k2;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = ti * kGT + ty * 4 + u, j = tj * kGT + tx * 4 + v;
+      if (i < k1 && j < k2) out[(size_t)i * k2 + j] = (double)acc[u][v];
+    }
+}
+
+__global__ void gram_reduce_kernel(int k1, int k2, int nz, bool sym, const double *work, double *C, int ldc,
+                                   const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)k1 * k2) return;
   int i = (int)(t / k2), j = (int)(t % k2);
@@ -180,14 +230,15 @@ static int gram_chunks(int64_t n, int k1, int k2) {
 size_t gram_work_doubles(int64_t n, int k1, int k2) { return (size_t)gram_chunks(n, k1, k2) * k1 * k2; }
 
 void gram(int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2, double *C, int ldc,
-          bool sym, double *work, cudaStream_t st) {
+          bool sym, double *work, cudaStream_t st, bool fp32, const int *run_if) {
   if (k1 <= 0 || k2 <= 0) return;
   const int nz = gram_chunks(n, k1, k2);
   const int64_t rpc = (n + nz - 1) / nz;
   dim3 grid((k1 + kGT - 1) / kGT, (k2 + kGT - 1) / kGT, nz);
-  gram_partial_kernel<<<grid, 256, 0, st>>>(n, X, ldx, k1, Y, ldy, k2, rpc, sym, work);
+  if (fp32) gram32_partial_kernel<<<grid, 256, 0, st>>>(n, X, ldx, k1, Y, ldy, k2, rpc, sym, work, run_if);
+  else gram_partial_kernel<<<grid, 256, 0, st>>>(n, X, ldx, k1, Y, ldy, k2, rpc, sym, work, run_if);
   const int64_t tot = (int64_t)k1 * k2;
-  gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k1, k2, nz, sym, work, C, ldc);
+  gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k1, k2, nz, sym, work, C, ldc, run_if);
 }
 
 // ------------------------------------------------------------------------------ GEMM
@@ -253,8 +304,10 @@ void gemm_nn(int64_t n, const double *X, int ldx, int k1, const double *S, int l
 // place), then the columns of L^{-1} by forward substitution (one warp per column),
 // stored transposed as R^{-1} = (L^{-1})^T.
 __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ldg, double *Rinv, int ldr,
-                                                        int *status) {
+                                                        int *status, const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   __shared__ int fail;
+  __shared__ double colj[512];  // column j of L below the diagonal (k <= 512)
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
   for (int j = 0; j < k; ++j) {
@@ -266,14 +319,18 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ld
     __syncthreads();
     if (fail) break;
     const double piv = G[(size_t)j * ldg + j];
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(size_t)i * ldg + j] /= piv;
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      const double lij = G[(size_t)i * ldg + j] / piv;
+      G[(size_t)i * ldg + j] = lij;
+      colj[i] = lij;
+    }
     __syncthreads();
     // trailing update of the lower triangle: G[i][l] -= L[i][j] L[l][j], j < l <= i
     {
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int i = j + 1 + warp; i < k; i += nw) {
-        const double lij = G[(size_t)i * ldg + j];
-        for (int l = j + 1 + lane; l <= i; l += 32) G[(size_t)i * ldg + l] -= lij * G[(size_t)l * ldg + j];
+        const double lij = colj[i];
+        for (int l = j + 1 + lane; l <= i; l += 32) G[(size_t)i * ldg + l] -= lij * colj[l];
       }
     }
     __syncthreads();
@@ -303,8 +360,8 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ld
   // *status is only ever raised (a failure of an earlier pass must survive).
 }
 
-void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st) {
-  chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, ldg, Rinv, ldr, status);
+void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st, const int *run_if) {
+  chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
 }
 
 // ------------------------------------------------------------------------------ Jacobi

@@ -18,8 +18,10 @@ void shifted_residual(int64_t n, int k, const double *AV, const double *BV, int 
 // C (k1 x k2, row-major, ldc) = X^T Y for X (n x k1), Y (n x k2).  sym: X == Y, k1 == k2,
 // only upper tiles are computed and mirrored.  work must hold gram_work_doubles(...) doubles.
 size_t gram_work_doubles(int64_t n, int k1, int k2);
+// fp32: FP32 inputs and accumulation within row chunks (for passes whose error a later
+// FP64 pass removes); run_if: device flag, the launch does nothing while *run_if == 0.
 void gram(int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2, double *C, int ldc,
-          bool sym, double *work, cudaStream_t st);
+          bool sym, double *work, cudaStream_t st, bool fp32 = false, const int *run_if = nullptr);
 
 // Z = alpha X S + beta Z;  X n x k1, S k1 x k2 (row-major, lds), Z n x k2.  upper: S is
 // upper triangular.  Z must not alias X.
@@ -28,7 +30,8 @@ void gemm_nn(int64_t n, const double *X, int ldx, int k1, const double *S, int l
 
 // G = R^T R (lower Cholesky L = R^T of the symmetric k x k G, using its lower triangle);
 // Rinv (k x k row-major, upper) = R^{-1}.  *status = 0 or SLRF_ECHOL (device int).
-void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st);
+void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st,
+              const int *run_if = nullptr);
 
 // Symmetric eigen-decomposition of H (k x k) by parallel cyclic Jacobi:
 // theta ascending (k), S (k x k row-major, column i = eigenvector i).

@@ -431,18 +431,24 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   const cudaStream_t st = ctx->st;
   const int64_t n = ctx->n;
   const int L = ctx->L;
-  ctx->launches += (nconv > 0 ? 6 : 0) + 19 + (want_basis ? 1 : 0);
+  ctx->launches += (nconv > 0 ? 6 : 0) + 22 + (want_basis ? 1 : 0);
+  // First passes in FP32 (mixed-precision CGS2 and Cholesky-QR): their Gram matrices only
+  // have to bring U close to the target; the FP64 second passes remove the FP32 error.
   if (nconv > 0) {
     for (int pass = 0; pass < 2; ++pass) {
-      gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st);
+      gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st, pass == 0);
       gemm_nn(n, X, ldx, nconv, ctx->Wm, k, k, U, L, -1.0, 1.0, false, st);
     }
   }
   double *U1 = ctx->U2, *AU1 = ctx->AG;
-  // pass 1: U1 = U R1^{-1}
+  // pass 1: U1 = U R1^{-1}, R1 from the FP32 Gram; if that Gram is not numerically
+  // positive definite (kappa(U) beyond ~1e3), iflags[11] triggers the FP64 Gram instead
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st);
-  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
-  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st);
+  cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
+  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st, true);
+  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st);
+  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st, false, ctx->iflags + 11);
+  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st, ctx->iflags + 11);
   gemm_nn(n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true, st);
   // pass 2 and projection
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U1, L, k, AU1, ctx->BU, L, st);
@@ -657,7 +663,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   ctx->m = o.m;
   ctx->mp = pow2_at_least(o.m);
   ctx->mixed = o.precision == 1;
-  ctx->vec = ctx->mixed ? 2 : 1;
+  ctx->vec = ctx->mixed ? cocg_vec<float>() : cocg_vec<double>();
   const int64_t n = ctx->n;
   const int L = block_L;
   const int kp = kpad_of(L, ctx->mp, ctx->vec);

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libslrf.so")
+_LIB_PATH = os.environ.get("SLRF_LIB", os.path.join(_HERE, "libslrf.so"))
 
 SLRF_OK = 0
 SLRF_EINVAL = -1
