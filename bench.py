@@ -155,6 +155,8 @@ def main():
     ap.add_argument("--it-max", type=int, default=None)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="batch64: also time the plain FP64 batched solve")
     ap.add_argument("--mixed-it-max", type=int, default=15,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
     args = ap.parse_args()
@@ -165,6 +167,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "batch64":
+        return batch_bench(args, rank, world, local)
 
     import numpy as np
     import torch
@@ -312,6 +316,82 @@ def main():
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def batch_bench(args, rank, world, local):
+    """64 uneven scalar Q1 pencils (slrf_inputs.batch) solved together: the COCG phases of
+    all problems in one persistent launch per phase.  A step = one batched solve."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import __graft_entry__ as ge
+
+    ge.build()
+    import slrf_inputs as si
+    from slrf_inputs import batch as sb
+    from paper_2510_17334_gb300 import slrf
+
+    specs = sb.batch_specs()
+    gam = sb.batch_gammas()
+    pens = [sb.batch_pencil(s) for s in specs]
+    probs = [(p.rowptr, p.col, p.valA, p.valB) for p in pens]
+    gammas = [g for g, _ in gam]
+    counts = [c for _, c in gam]
+    blocks = [int(np.ceil(1.5 * c)) for c in counts]
+    V0 = [torch.from_numpy(si.start_block(p.n, L, s.seed)).cuda() for p, L, s in zip(pens, blocks, specs)]
+    stream = torch.cuda.Stream()
+
+    def run(precision, it_max):
+        opts = slrf.slrf_opts_default(it_max=it_max, precision=precision, autotune=1)
+        with torch.cuda.stream(stream):
+            b = slrf.Batch(probs, gammas, blocks, opts, stream=stream)
+            for _ in range(args.warmup):
+                b.solve(V0, check=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            found = 0
+            for _ in range(args.steps):
+                rc, res, st = b.solve(V0, check=False)
+                found += sum(r[1] for r in res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            exact = sum(1 for r, c in zip(res, counts) if r[1] == c)
+            maxres = max(float(r[4].max().item()) for r in res if r[1] > 0)
+            evs = [r[2].cpu().numpy() for r in res]
+            b.close()
+        return {"value": found / (ms / 1e3), "ms_per_step": ms / args.steps, "rc": rc,
+                "problems_with_exact_count": exact, "eigenpairs": found // args.steps, "max_resid": maxres,
+                "outer_iters_max": st["outer_iters"], "column_iterations": st["column_iterations"],
+                "kernel_launches": st["kernel_launches"], "it_max": it_max}, evs
+
+    cp, cf = clocks_start()
+    prec = 1 if args.precision == 0 and not args.compare_fp64 else args.precision
+    main, evs_main = run(1, args.mixed_it_max if args.it_max is None else args.it_max)
+    clk = clocks_stop(cp, cf, local)
+    fp64 = None
+    if args.compare_fp64:
+        fp64, evs64 = run(0, args.it_max or args.mixed_it_max)
+        diffs = [float(np.max(np.abs(a - b) / np.abs(b))) for a, b in zip(evs_main, evs64) if len(a) == len(b) and len(a)]
+        fp64["max_rel_eig_diff_mixed_vs_fp64"] = max(diffs) if diffs else None
+    ntot = sum(p.n for p in pens)
+    line = {"metric": METRIC, "value": main["value"], "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c32-in-f64", "data": "synthetic",
+            "config": {"workload": (f"batch64: 64 uneven scalar Q1 pencils (2D/3D, lognormal(0,0.3) coefficients, "
+                                    f"sum n = {ntot}, {sum(counts)} eigenpairs, blocks 1.5x count, m=8), "
+                                    f"one persistent COCG launch per phase"),
+                       "precision": "mixed (complex-FP32 COCG, FP64 outer)", "autotune": 1},
+            "batched_mixed": main, "batched_fp64": fp64, "gpu_launches": main["kernel_launches"], "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def cpu_baseline_subprocess(name, it_max, n_found, col_iters, outer):

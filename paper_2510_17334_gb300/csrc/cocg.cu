@@ -23,6 +23,13 @@
 // them in a fixed order (deterministic) and updates the per-column scalars.
 #include "cocg.cuh"
 
+#ifndef SLRF_SPMM_ROW2
+#define SLRF_SPMM_ROW2 0
+#endif
+#ifndef SLRF_SPMM_PREFETCH
+#define SLRF_SPMM_PREFETCH 0
+#endif
+
 namespace slrf {
 
 template <typename R> struct Vec;
@@ -361,8 +368,8 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   if (warp_act) {
-    for (int64_t i = i0 + warp; i < i1; i += kWarps) {
-      C sa[VEC], sb[VEC];
+    // s = (A - sigma B) r for one row (sa = A r, sb = B r), lanes over this warp's columns
+    auto gather_row = [&](int64_t i, C (&sa)[VEC], C (&sb)[VEC]) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) { sa[v] = cmake<C>(0, 0); sb[v] = cmake<C>(0, 0); }
       const int64_t rs = a.rowptr[i], re = a.rowptr[i + 1];
@@ -386,12 +393,10 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
           }
         }
       }
+    };
+    // p = r + beta p, q = s + beta q for the row, and its mu partial
+    auto finish_row = [&](int64_t i, const C (&sa)[VEC], const C (&sb)[VEC], const Vec<R> &rv, Vec<R> pv, Vec<R> qv) {
       const size_t off = (size_t)i * a.W + w0;
-      Vec<R> rv = ldv<R>(a.r + off), pv, qv;
-      if (!FRESH) {
-        pv = ldv<R>(a.p + off);
-        qv = ldv<R>(a.q + off);
-      }
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         const C s = cfms(sg[v], sb[v], sa[v]);  // A r - sigma B r
@@ -405,7 +410,43 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
       }
       stv<R>(a.p + off, pv);
       stv<R>(a.q + off, qv);
+    };
+    auto load_own = [&](int64_t i, Vec<R> &rv, Vec<R> &pv, Vec<R> &qv) {
+      const size_t off = (size_t)i * a.W + w0;
+      rv = ldv<R>(a.r + off);
+      if (!FRESH) {
+        pv = ldv<R>(a.p + off);
+        qv = ldv<R>(a.q + off);
+      }
+    };
+#if SLRF_SPMM_ROW2
+    for (int64_t i = i0 + warp; i < i1; i += 2 * kWarps) {
+      const int64_t i2 = i + kWarps;
+      C sa[VEC], sb[VEC], sa2[VEC], sb2[VEC];
+      gather_row(i, sa, sb);
+      if (i2 < i1) gather_row(i2, sa2, sb2);
+      Vec<R> rv, pv, qv;
+      load_own(i, rv, pv, qv);
+      finish_row(i, sa, sb, rv, pv, qv);
+      if (i2 < i1) {
+        load_own(i2, rv, pv, qv);
+        finish_row(i2, sa2, sb2, rv, pv, qv);
+      }
     }
+#else
+    for (int64_t i = i0 + warp; i < i1; i += kWarps) {
+      C sa[VEC], sb[VEC];
+      Vec<R> rv, pv, qv;
+#if SLRF_SPMM_PREFETCH
+      load_own(i, rv, pv, qv);
+      gather_row(i, sa, sb);
+#else
+      gather_row(i, sa, sb);
+      load_own(i, rv, pv, qv);
+#endif
+      finish_row(i, sa, sb, rv, pv, qv);
+    }
+#endif
   }
   double out[NQ];
   int w;
