@@ -31,8 +31,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clock x 2 flo
 # Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
 # over all (pole, column) systems and outer iterations), used to scale the timed oracle
 # sample of the reference arm to a whole solve.
-SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 18, "column_iterations": 326400},
-                "bar1d_2000": {"n_found": 20, "outer": 8, "column_iterations": 358400}}
+SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 17, "column_iterations": 166560},
+                "bar1d_2000": {"n_found": 20, "outer": 8, "column_iterations": 358400},
+                "elast_32": {"n_found": 60, "outer": 20, "column_iterations": 448640}}
 
 
 def workload(name: str, it_max: int | None):
@@ -49,6 +50,15 @@ def workload(name: str, it_max: int | None):
         wl.it_max = it_max or 40
         desc = (f"3D Q1 Laplacian + consistent mass, {nodes}^3 nodes (n={wl.n}), Neumann + 1e-3 B, "
                 f"gamma={wl.gamma:.4f} ({wl.n_expected} eigenpairs), block {wl.block}, m=8")
+    elif name in ("elast_32", "elast_48"):
+        from slrf_inputs import elastic as se
+
+        p = se.pencil(name)
+        g, cnt = se.gamma(name)
+        spec = se.SPECS[name]
+        wl = si.Workload(name, p, g, spec["block"], 8, spec["seed"], it_max or 40, cnt)
+        desc = (f"3D Q1 elasticity {spec['nodes']} nodes, z=0 clamped (n={p.n}, nnz={p.nnz}), E lognormal(0,0.5), "
+                f"nu=0.3, gamma={g:.4f} ({cnt} eigenpairs), block {spec['block']}, m=8")
     elif name == "bar1d_2000":
         wl = si.bar1d(2000)
         wl.it_max = it_max or 200
