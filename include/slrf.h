@@ -64,13 +64,13 @@ typedef struct {
   double alpha;           /* pole line slope: sigma = Re(sigma)(1 + alpha i), default 1     */
   double beta;            /* relaxation (Tikhonov) weight of the pole design, default 0.01  */
   double band;            /* stop band starts at band*gamma, default 1.3                    */
-  int it_max;             /* It_max-linear: fixed COCG updates per solve (Alg. 2 l.10)     */
+  int it_max;             /* It_max-linear: fixed COCG updates per solve (Alg. 2)     */
   int refine_max;         /* mixed path: refinement steps (FP64 residual + FP32 solve), >= 1 */
   int outer_max;          /* outer iteration cap, default 100                               */
   double tol_inner;       /* COCG stop ||r|| <= tol_inner ||r0||, default 1e-10 (Sec. 3.2)  */
   double tol_eig;         /* lock when ||Av - theta Bv|| / ||Av|| <= tol_eig, default 1e-8  */
   int precision;          /* 0 = FP64 throughout; 1 = complex-FP32 COCG in FP64 refinement  */
-  int warm_start;         /* 1 = y0 = v/(theta - sigma) (Alg. 2 l.21); 0 = y0 = 0           */
+  int warm_start;         /* 1 = y0 = v/(theta - sigma) (Alg. 2); 0 = y0 = 0           */
   int lock;               /* 1 = lock converged pairs (Alg. 2); 0 = basic method (Alg. 1)   */
   int use_graph;          /* 1 = replay the It_max inner loop from a captured CUDA graph    */
   int nev;                /* if > 0, also require this many locked pairs before stopping    */
@@ -78,6 +78,8 @@ typedef struct {
   const double *poles;    /* optional HOST table: m complex poles, (re, im) interleaved     */
   const double *weights;  /* optional HOST table: m complex weights; NULL = SLRF design     */
   int autotune;           /* 1 = time candidate COCG rows-per-block at setup, keep the fastest */
+  int dense;              /* products of the outer update: 1 = split-bf16 tensor-core products
+                             with FP64 error (Ozaki splitting), 0 = FP64 FMA; default 1     */
 } slrf_opts;
 
 /* Statistics of the last slrf_solve (host struct filled by the library). */
@@ -98,7 +100,8 @@ typedef struct {
 /* Fill *opts with the paper's defaults: m = 8, alpha = 1, beta = 0.01 (Sec. 3.2),
  * band = 1.3, it_max = 40, refine_max = 1, outer_max = 100, tol_inner = 1e-10 (Sec. 3.2),
  * tol_eig = 1e-8 (Sec. 3.2), precision = 0, warm_start = 1, lock = 1 (Sec. 4), use_graph = 1,
- * nev = 0, seed = 1, poles = weights = NULL.  Returns SLRF_EINVAL if opts is NULL. */
+ * nev = 0, seed = 1, poles = weights = NULL, autotune = 0, dense = 1.  Returns SLRF_EINVAL
+ * if opts is NULL. */
 int slrf_opts_default(slrf_opts *opts);
 
 /* Create a solver context for the pencil (A, B), the interval (0, gamma] and search-block
@@ -116,11 +119,11 @@ int slrf_setup(slrf_ctx **ctx, const slrf_csr_pair *pencil, double gamma, int bl
  * receives m.  Synchronises the stream. */
 int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w);
 
-/* Apply the rational filter to a real block (Alg. 2 lines 7-14):
+/* Apply the rational filter to a real block (the filter step of Alg. 2):
  *   U = sum_{j=1..m} 2 Re(w_j Y_j),   (A - sigma_j B) Y_j = B X,
  * every (pole, column) system solved by COCG for at most it_max updates or until
  * ||r|| <= tol_inner ||r0||.  X (device, n x k row-major) is the block, k <= L.  theta
- * (device, k entries) gives the warm start y0 = x_c / (theta_c - sigma_j) (Alg. 2 l.21,
+ * (device, k entries) gives the warm start y0 = x_c / (theta_c - sigma_j) (Alg. 2,
  * the Cayley form of the Proposition, Sec. 4); theta = NULL gives y0 = 0.  U (device,
  * n x k row-major) receives the filtered block and may not alias X.  Precision follows
  * opts.precision: with precision = 1 the solve runs in FP64 iterative refinement --
@@ -145,7 +148,7 @@ int slrf_filter_timing(slrf_ctx *ctx, const double *X, int k, const double *thet
  * breakdown flag.  Any pointer may be NULL.  Synchronises the stream. */
 int slrf_filter_stats(slrf_ctx *ctx, int *iters, double *relres, int *breakdown);
 
-/* B-orthonormalise and project one filtered block (Alg. 2 lines 15-18):
+/* B-orthonormalise and project one filtered block (the outer update of Alg. 2):
  *   if n_conv > 0:  U <- U - X (BX^T U), twice (CGS2 against the locked vectors);
  *   G = U^T B U = R^T R, U <- U R^{-1}, twice (Cholesky-QR2);
  *   H = U^T A U = S diag(theta) S^T, theta ascending;  V = U S;
@@ -249,6 +252,28 @@ int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, in
  * SLRF_ECUDA. */
 int slrf_filter_apply_static(const slrf_csr_pair *pencil, double gamma, const slrf_opts *opts,
                              const double *X, int k, const double *theta, double *U, void *stream);
+
+/* Tall-skinny FP64 products of the outer update (the X^T B U, U^T B U, U^T A U Gram
+ * matrices and the U R^{-1}, U S projections of Alg. 2), as the solver computes them:
+ *   slrf_tsgram:  C (k1 x k2, leading dimension ldc) = X^T Y,
+ *                 X (n x k1, ldx), Y (n x k2, ldy);
+ *   slrf_tsgemm:  Z (n x k2, ldz) = alpha X S + beta Z,
+ *                 X (n x k1, ldx), S (k1 x k2, lds); Z may not alias X.
+ * All device pointers, FP64, row-major.  mode 1: split-bf16 tensor-core products -- each
+ * entry is written, against the largest exponent of its row of X^T (its column of Y), as
+ * 7 balanced 8-bit digits held exactly in bf16; the digit products of the five leading
+ * significance levels are summed exactly (FP32 tensor-core sums below 2^24 units over
+ * blocks of 128 products, then 64-bit integers), the next two levels in FP32, the rest
+ * (below 2^-56 of the leading term) dropped, so the error is that of an FP64 product.
+ * mode 0: FP64 FMA on the CUDA cores.  1 <= k1, k2 <= 512, n >= 0 (n = 0 gives C = 0, and
+ * X, Y, Z may then be NULL).
+ * The call allocates its workspace on the stream (a cudaStream_t or NULL), frees it and
+ * synchronises the stream.  Errors: SLRF_EINVAL, SLRF_ENOMEM, SLRF_ETIMEOUT (a bounded
+ * device-side wait gave up), SLRF_ECUDA. */
+int slrf_tsgram(int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2, double *C,
+                int ldc, int mode, void *stream);
+int slrf_tsgemm(int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2, double *Z,
+                int ldz, double alpha, double beta, int mode, void *stream);
 
 /* Release the context and all its device memory.  NULL is accepted. */
 void slrf_destroy(slrf_ctx *ctx);

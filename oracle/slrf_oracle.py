@@ -154,10 +154,10 @@ class FilterInfo:
 
 
 def filter_apply(A, B, V, theta, sigma, w, it_max, tol):
-    """Apply the rational filter to the real block V (n x k), Alg. 2 lines 7-14.
+    """Apply the rational filter to the real block V (n x k), the filter step of Alg. 2.
 
     ``theta`` = None gives the zero initial guess; otherwise column c starts from
-    y0 = v_c / (theta_c - sigma_j) (Alg. 2 line 21).  All m x k systems are solved
+    y0 = v_c / (theta_c - sigma_j) (the warm start of Alg. 2).  All m x k systems are solved
     side by side as independent columns, pole-major: column j*k + c is pole j, vector c.
     """
     n, k = V.shape
@@ -179,7 +179,7 @@ def filter_apply(A, B, V, theta, sigma, w, it_max, tol):
 
 
 # ----------------------------------------------------------------------------------------
-# a6: B-orthogonalise against the locked vectors (Alg. 2 lines 15-17), CGS2
+# a6: B-orthogonalise against the locked vectors (first step of the outer update of Alg. 2), CGS2
 # ----------------------------------------------------------------------------------------
 def b_orth(U, X, BX):
     """U <- U - X (X^T B U), twice, using the stored B X."""
@@ -205,7 +205,7 @@ def cholqr2(U, B):
 
 
 # ----------------------------------------------------------------------------------------
-# a8: Rayleigh-Ritz on the B-orthonormal basis (Alg. 2 line 18)
+# a8: Rayleigh-Ritz on the B-orthonormal basis (Alg. 2)
 # ----------------------------------------------------------------------------------------
 def rayleigh_ritz(U, A):
     """theta ascending and V = U S from the eigenpairs of H = U^T A U."""

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.environ.get("SLRF_BUILD_DIR", os.path.join(HERE, "_build"))
 ROOT = os.path.dirname(HERE)
 LIB = os.environ.get("SLRF_LIB", os.path.join(HERE, "libslrf.so"))
-SOURCES = ["cocg.cu", "dense.cu", "adjoint.cu", "slrf.cu", "static_filter.cu"]
+SOURCES = ["cocg.cu", "dense.cu", "ozaki.cu", "adjoint.cu", "slrf.cu", "static_filter.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"] + os.environ.get("SLRF_NVCC_DEFINES", "").split()

@@ -1,4 +1,4 @@
-// FP64 kernels of the outer iteration (arXiv 2510.17334, Alg. 2 lines 15-21): real SpMM,
+// FP64 kernels of the outer iteration (arXiv 2510.17334, Alg. 2: B-orthonormalisation, Rayleigh-Ritz, locking): real SpMM,
 // tall-skinny Gram and GEMM products, Cholesky-QR building blocks, the projected
 // symmetric eigenproblem (parallel cyclic Jacobi), Ritz residuals and locking.
 // GB300 executes FP64 at about 2 FMA/clock/SM, so these kernels spread the FP64 work over

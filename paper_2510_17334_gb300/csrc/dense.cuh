@@ -1,5 +1,5 @@
 // FP64 kernels of the outer iteration: real SpMM, tall-skinny products, small dense
-// factorisations, Ritz residuals and locking (arXiv 2510.17334, Alg. 2 lines 15-21).
+// factorisations, Ritz residuals and locking (arXiv 2510.17334, Alg. 2: B-orthonormalisation, Rayleigh-Ritz, locking).
 #pragma once
 
 #include "common.cuh"

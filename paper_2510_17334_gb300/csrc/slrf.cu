@@ -3,9 +3,9 @@
 // The paper's two parallel levels (poles across process groups, each solve across the
 // processes of a group; Sec. 2.1) become one grid: every (pole, column) system of a
 // filter apply is in flight in the same COCG launches, and the paper's sum-reduce of
-// the Y_j (Alg. 2 line 14) is the in-register pole sum of the last COCG update.
+// the Y_j (the filter sum of Alg. 2) is the in-register pole sum of the last COCG update.
 // The host drives the outer loop; the only device->host transfer per outer iteration is
-// a handful of integers for the lock decision (Alg. 2 lines 19-20).
+// a handful of integers for the lock decision (the locking step of Alg. 2).
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -18,6 +18,7 @@
 #include "../../include/slrf.h"
 #include "cocg.cuh"
 #include "dense.cuh"
+#include "ozaki.cuh"
 
 using namespace slrf;
 
@@ -84,6 +85,8 @@ struct slrf_ctx {
   double *Theta = nullptr, *Res = nullptr;
   double *work = nullptr;
   size_t work_doubles = 0;
+  unsigned char *ozwork = nullptr;  // split-bf16 product workspace (opts.dense = 1)
+  size_t ozwork_bytes = 0;
   int *dst_x = nullptr, *dst_v = nullptr, *iflags = nullptr;  // iflags: [0..3] lock info, [4] chol, [5] nan
   int *h_iflags = nullptr;                                    // pinned mirror
   JacobiWork jw{};
@@ -418,6 +421,34 @@ static int autotune_rows(slrf_ctx *ctx) {
   return SLRF_OK;
 }
 
+// ----------------------------------------------------------------------------- products
+// Tall-skinny products of the outer update: split-bf16 tensor-core products with the error
+// of an FP64 product (opts.dense = 1) or FP64 FMA on the CUDA cores.  FP32 first passes
+// stay on the CUDA cores.  Each adds the kernels it launches to ctx->launches.
+static void tsgram(slrf_ctx *ctx, int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2,
+                   double *C, int ldc, bool sym, bool fp32 = false, const int *run_if = nullptr) {
+  if (ctx->ozwork && !fp32) {
+    const bool same = X == Y && ldx == ldy && k1 == k2;
+    oz_gram(n, X, ldx, k1, Y, ldy, k2, C, ldc, sym, ctx->ozwork, ctx->ozwork_bytes, ctx->iflags + 13, ctx->st,
+            run_if);
+    ctx->launches += same ? 4 : 6;
+  } else {
+    gram(n, X, ldx, k1, Y, ldy, k2, C, ldc, sym, ctx->work, ctx->st, fp32, run_if);
+    ctx->launches += 2;
+  }
+}
+static void tsgemm(slrf_ctx *ctx, int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2,
+                   double *Z, int ldz, double alpha, double beta, bool upper) {
+  if (ctx->ozwork) {
+    oz_gemm(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, ctx->ozwork, ctx->ozwork_bytes, ctx->iflags + 13,
+            ctx->st);
+    ctx->launches += 4;
+  } else {
+    gemm_nn(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, upper, ctx->st);
+    ctx->launches += 1;
+  }
+}
+
 // ----------------------------------------------------------------------------- RR step
 // U (n x k, ld L) -> B-orth vs X (CGS2) -> Cholesky-QR2 -> Rayleigh-Ritz -> Vt, AVt, BVt,
 // theta, res, res_paper, sgn.  The second CholQR pass is folded into the projection:
@@ -431,13 +462,13 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   const cudaStream_t st = ctx->st;
   const int64_t n = ctx->n;
   const int L = ctx->L;
-  ctx->launches += (nconv > 0 ? 6 : 0) + 22 + (want_basis ? 1 : 0);
+  ctx->launches += 9;  // 3 real SpMMs, 3 Cholesky, Jacobi, 2 residual kernels; products count themselves
   // First passes in FP32 (mixed-precision CGS2 and Cholesky-QR): their Gram matrices only
   // have to bring U close to the target; the FP64 second passes remove the FP32 error.
   if (nconv > 0) {
     for (int pass = 0; pass < 2; ++pass) {
-      gram(n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, ctx->work, st, pass == 0);
-      gemm_nn(n, X, ldx, nconv, ctx->Wm, k, k, U, L, -1.0, 1.0, false, st);
+      tsgram(ctx, n, BX, ldx, nconv, U, L, k, ctx->Wm, k, false, pass == 0);
+      tsgemm(ctx, n, X, ldx, nconv, ctx->Wm, k, k, U, L, -1.0, 1.0, false);
     }
   }
   double *U1 = ctx->U2, *AU1 = ctx->AG;
@@ -445,24 +476,24 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   // positive definite (kappa(U) beyond ~1e3), iflags[11] triggers the FP64 Gram instead
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st);
   cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
-  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st, true);
+  tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, true);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st);
-  gram(n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st, false, ctx->iflags + 11);
+  tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, false, ctx->iflags + 11);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st, ctx->iflags + 11);
-  gemm_nn(n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true, st);
+  tsgemm(ctx, n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true);
   // pass 2 and projection
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U1, L, k, AU1, ctx->BU, L, st);
-  gram(n, U1, L, k, ctx->BU, L, k, ctx->Gm, k, true, ctx->work, st);
-  gram(n, U1, L, k, AU1, L, k, ctx->Hm, k, true, ctx->work, st);
+  tsgram(ctx, n, U1, L, k, ctx->BU, L, k, ctx->Gm, k, true);
+  tsgram(ctx, n, U1, L, k, AU1, L, k, ctx->Hm, k, true);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st);
-  gemm_nn(k, ctx->Hm, k, k, ctx->Rinv, k, k, ctx->Wm, k, 1.0, 0.0, true, st);  // T = H1 R2^{-1}
-  gram(k, ctx->Rinv, k, k, ctx->Wm, k, k, ctx->Gm, k, true, ctx->work, st);       // H = R2^{-T} T
+  tsgemm(ctx, k, ctx->Hm, k, k, ctx->Rinv, k, k, ctx->Wm, k, 1.0, 0.0, true);  // T = H1 R2^{-1}
+  tsgram(ctx, k, ctx->Rinv, k, k, ctx->Wm, k, k, ctx->Gm, k, true);           // H = R2^{-T} T
   CKL();
   int rc = jacobi_eig(k, ctx->Gm, k, ctx->theta, ctx->Sm, k, ctx->jw, st);
   if (rc != SLRF_OK) { ctx->status = rc; return rc; }
-  gemm_nn(k, ctx->Rinv, k, k, ctx->Sm, k, k, ctx->Wm, k, 1.0, 0.0, false, st);  // Z = R2^{-1} S
-  gemm_nn(n, U1, L, k, ctx->Wm, k, k, ctx->Vt, L, 1.0, 0.0, false, st);         // V = U1 Z
-  if (want_basis) gemm_nn(n, U1, L, k, ctx->Rinv, k, k, U, L, 1.0, 0.0, true, st);
+  tsgemm(ctx, k, ctx->Rinv, k, k, ctx->Sm, k, k, ctx->Wm, k, 1.0, 0.0, false);  // Z = R2^{-1} S
+  tsgemm(ctx, n, U1, L, k, ctx->Wm, k, k, ctx->Vt, L, 1.0, 0.0, false);         // V = U1 Z
+  if (want_basis) tsgemm(ctx, n, U1, L, k, ctx->Rinv, k, k, U, L, 1.0, 0.0, true);
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
   ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
   CKL();
@@ -591,6 +622,7 @@ int slrf_opts_default(slrf_opts *o) {
   o->use_graph = 1;
   o->nev = 0;
   o->seed = 1;
+  o->dense = 1;
   return SLRF_OK;
 }
 
@@ -612,6 +644,57 @@ const char *slrf_strerror(int s) {
 }
 
 int slrf_last_error(const slrf_ctx *ctx) { return ctx ? ctx->status : SLRF_EINVAL; }
+
+// ----------------------------------------------------------------------------- products (ABI)
+static int ts_prologue(int64_t n, int k1, int k2, int mode, cudaStream_t st, void **work, int **err,
+                       size_t bytes) {
+  if (n < 0 || k1 < 1 || k2 < 1 || k1 > 512 || k2 > 512 || (mode != 0 && mode != 1)) return SLRF_EINVAL;
+  if (cudaMallocAsync(work, bytes + 64, st) != cudaSuccess) { cudaGetLastError(); return SLRF_ENOMEM; }
+  if (cudaMallocAsync(reinterpret_cast<void **>(err), sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(*work, st);
+    return SLRF_ENOMEM;
+  }
+  cudaMemsetAsync(*err, 0, sizeof(int), st);
+  return SLRF_OK;
+}
+static int ts_epilogue(cudaStream_t st, void *work, int *err) {
+  int h = 0;
+  cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(work, st);
+  cudaFreeAsync(err, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
+  return h != 0 ? SLRF_ETIMEOUT : SLRF_OK;
+}
+
+int slrf_tsgram(int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2, double *C, int ldc,
+                int mode, void *stream) {
+  if ((n > 0 && (!X || !Y)) || !C || ldx < k1 || ldy < k2 || ldc < k2) return SLRF_EINVAL;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = mode == 1 ? oz_work_bytes(n, k1, k2)
+                                 : std::max<size_t>(gram_work_doubles(n, k1, k2), 1) * sizeof(double);
+  void *work = nullptr;
+  int *err = nullptr;
+  int rc = ts_prologue(n, k1, k2, mode, st, &work, &err, bytes);
+  if (rc != SLRF_OK) return rc;
+  if (mode == 1) oz_gram(n, X, ldx, k1, Y, ldy, k2, C, ldc, false, work, bytes, err, st);
+  else gram(n, X, ldx, k1, Y, ldy, k2, C, ldc, false, static_cast<double *>(work), st);
+  return ts_epilogue(st, work, err);
+}
+
+int slrf_tsgemm(int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2, double *Z, int ldz,
+                double alpha, double beta, int mode, void *stream) {
+  if ((n > 0 && (!X || !Z)) || !S || ldx < k1 || lds < k2 || ldz < k2 || (n > 0 && X == Z)) return SLRF_EINVAL;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *work = nullptr;
+  int *err = nullptr;
+  const size_t bytes = mode == 1 ? oz_work_bytes(n, k1, k2) : 64;
+  int rc = ts_prologue(n, k1, k2, mode, st, &work, &err, bytes);
+  if (rc != SLRF_OK) return rc;
+  if (mode == 1) oz_gemm(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, work, bytes, err, st);
+  else gemm_nn(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, false, st);
+  return ts_epilogue(st, work, err);
+}
 
 void slrf_destroy(slrf_ctx *ctx) {
   if (!ctx) return;
@@ -636,7 +719,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   slrf_opts o;
   if (opts) o = *opts;
   else slrf_opts_default(&o);
-  if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1) return SLRF_EINVAL;
+  if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1 || o.dense < 0 || o.dense > 1)
+    return SLRF_EINVAL;
   if (block_L > 510) return SLRF_EINVAL;  // the projected eigensolver holds two rows of <= 512 in shared memory
   if (!(o.tol_inner >= 0) || !(o.tol_eig > 0)) return SLRF_EINVAL;
   if (pc->n > (int64_t)INT32_MAX) return SLRF_EINVAL;  // int32 column indices
@@ -783,6 +867,10 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   // gram() splits rows into at most 64 chunks of k1 x k2 <= L x L partial tiles
   ctx->work_doubles = std::max({(size_t)64 * L * L, ritz_work_doubles(n, L), (size_t)4 * L});
   AL(ctx->work, ctx->work_doubles);
+  if (o.dense) {
+    ctx->ozwork_bytes = oz_work_bytes(n, L, L);
+    AL(ctx->ozwork, ctx->ozwork_bytes);
+  }
   {
     const int kk = L + (L & 1) < 2 ? 2 : L + (L & 1);
     AL(ctx->jw.A, (size_t)kk * kk);
@@ -892,6 +980,7 @@ int slrf_rayleigh_ritz(slrf_ctx *ctx, double *U, int k, const double *X, const d
   int hf[16];
   CK(cudaMemcpyAsync(hf, ctx->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (hf[9] != 0 || hf[13] != 0) return SLRF_ETIMEOUT;
   if (hf[4] != 0) return SLRF_ECHOL;
   // apply the sign convention and hand out V, theta, res
   {
@@ -949,7 +1038,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
     S.column_solves += (int64_t)ctx->m * k;
     rc = rr_impl(ctx, ctx->U, k, ctx->X, ctx->BX, ctx->o.lock ? nconv : 0, L);
     if (rc != SLRF_OK) return rc;
-    // lock decision, compaction (Alg. 2 lines 19-20)
+    // lock decision, compaction (the locking step of Alg. 2)
     lock_decide(k, ctx->theta, ctx->res, ctx->gamma, ctx->o.tol_eig, ctx->o.lock, L, ctx->iflags, ctx->dst_x,
                 ctx->dst_v, ctx->Theta, ctx->Res, ctx->theta_act, st);
     lock_gather(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->sgn, ctx->dst_x, ctx->dst_v, ctx->X, ctx->BX, L, ctx->V,
@@ -966,7 +1055,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
       ms_d += b;
     }
     const int *hf = ctx->h_iflags;
-    if (hf[9] != 0) { status = SLRF_ETIMEOUT; break; }
+    if (hf[9] != 0 || hf[13] != 0) { status = SLRF_ETIMEOUT; break; }
     if (hf[4] != 0) { status = SLRF_ECHOL; break; }
     nconv = hf[0];
     k = hf[1];
@@ -1166,7 +1255,7 @@ int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, 
       CK(cudaStreamSynchronize(c->st));
       const int *hf = c->h_iflags;
       outer_of[p] = outer;
-      if (hf[9] != 0) { st_p[p] = SLRF_ETIMEOUT; done[p] = 1; continue; }
+      if (hf[9] != 0 || hf[13] != 0) { st_p[p] = SLRF_ETIMEOUT; done[p] = 1; continue; }
       if (hf[4] != 0) { st_p[p] = SLRF_ECHOL; done[p] = 1; continue; }
       nconv[p] = hf[0];
       kk[p] = hf[1];

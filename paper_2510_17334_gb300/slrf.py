@@ -32,7 +32,7 @@ SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_app
            "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
            "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static", "slrf_setup_batched",
-           "slrf_solve_batched", "slrf_destroy_batched")
+           "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm")
 
 
 class SlrfError(RuntimeError):
@@ -51,7 +51,8 @@ class Opts(ct.Structure):
                 ("it_max", ct.c_int), ("refine_max", ct.c_int), ("outer_max", ct.c_int),
                 ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
                 ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
-                ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int)]
+                ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int),
+                ("dense", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -90,6 +91,8 @@ def lib() -> ct.CDLL:
         L.slrf_destroy_batched.argtypes = [vp]
         L.slrf_destroy_batched.restype = None
         L.slrf_filter_apply_static.argtypes = [ct.POINTER(CsrPair), d, ct.POINTER(Opts), vp, i, vp, vp, vp]
+        L.slrf_tsgram.argtypes = [i64, vp, i, i, vp, i, i, vp, i, i, vp]
+        L.slrf_tsgemm.argtypes = [i64, vp, i, i, vp, i, i, vp, i, d, d, i, vp]
         L.slrf_destroy.argtypes = [vp]
         L.slrf_destroy.restype = None
         L.slrf_strerror.argtypes = [i]
@@ -311,6 +314,34 @@ class Batch:
             c = min(int(nf[i]), int(caps[i]))
             out.append((int(stt[i]), int(nf[i]), ev[i][:c], X[i][:, :c], rs[i][:c]))
         return rc, out, st.as_dict()
+
+
+def tsgram(X: torch.Tensor, Y: torch.Tensor, mode: int = 1) -> torch.Tensor:
+    """slrf_tsgram: C = X^T Y for device FP64 row-major blocks X (n x k1), Y (n x k2);
+    mode 1 = split-bf16 tensor-core products, 0 = FP64 FMA."""
+    assert X.is_cuda and Y.is_cuda and X.dtype == torch.float64 and Y.dtype == torch.float64
+    assert X.shape[0] == Y.shape[0] and X.stride(1) == 1 and Y.stride(1) == 1
+    k1, k2 = X.shape[1], Y.shape[1]
+    C = torch.empty(k1, k2, dtype=torch.float64, device=X.device)
+    st = torch.cuda.current_stream(X.device)
+    _check(lib().slrf_tsgram(X.shape[0], _ptr(X), X.stride(0), k1, _ptr(Y), Y.stride(0), k2, _ptr(C), k2, int(mode),
+                             ct.c_void_p(st.cuda_stream)), "slrf_tsgram")
+    return C
+
+
+def tsgemm(X: torch.Tensor, S: torch.Tensor, Z: torch.Tensor | None = None, alpha: float = 1.0, beta: float = 0.0,
+           mode: int = 1) -> torch.Tensor:
+    """slrf_tsgemm: Z = alpha X S + beta Z for device FP64 row-major X (n x k1), S (k1 x k2)."""
+    assert X.is_cuda and S.is_cuda and X.dtype == torch.float64 and S.dtype == torch.float64
+    assert X.shape[1] == S.shape[0] and X.stride(1) == 1 and S.stride(1) == 1
+    n, k2 = X.shape[0], S.shape[1]
+    if Z is None:
+        Z = torch.zeros(n, k2, dtype=torch.float64, device=X.device)
+    assert Z.shape == (n, k2) and Z.stride(1) == 1
+    st = torch.cuda.current_stream(X.device)
+    _check(lib().slrf_tsgemm(n, _ptr(X), X.stride(0), X.shape[1], _ptr(S), S.stride(0), k2, _ptr(Z), Z.stride(0),
+                             float(alpha), float(beta), int(mode), ct.c_void_p(st.cuda_stream)), "slrf_tsgemm")
+    return Z
 
 
 def filter_apply_static(rowptr, col, valA, valB, gamma, opts, X, theta=None, U=None, stream=None):

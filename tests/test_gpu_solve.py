@@ -33,13 +33,14 @@ def _solve(slrf, p, gamma, L, seed, **kw):
     return out
 
 
-def test_rayleigh_ritz_step_parity(slrf_mod):
+@pytest.mark.parametrize("dense", [1, 0])
+def test_rayleigh_ritz_step_parity(slrf_mod, dense):
     n, L = 500, 13
     p = si.bar1d_pencil(n)
     A, B = p.A(), p.B()
     lam, Xe = sla.eigh(A.toarray(), B.toarray())
     gamma = 0.5 * (lam[7] + lam[8])
-    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, slrf_mod.slrf_opts_default())
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, slrf_mod.slrf_opts_default(dense=dense))
     so, wo = orc.slrf_poles(8, gamma)
     Uo, _ = orc.filter_apply(A, B, si.start_block(n, L, 5), None, so, wo, 60, 1e-10)
     # without locked vectors
@@ -97,14 +98,15 @@ def test_solve_bar1d_2000_matches_closed_form_and_oracle(slrf_mod):
         assert abs(abs(s @ (B @ X[:, k])) - 1.0) <= 1e-9
 
 
+@pytest.mark.parametrize("dense", [1, 0])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_solve_q1_small(slrf_mod, precision):
+def test_solve_q1_small(slrf_mod, precision, dense):
     nodes = (13, 13, 13)
     p = si.q1_scalar(nodes, shift=1e-3)
     lam = pins.q1_neumann_eigs(nodes, 1e-3)
     gamma, cnt = pins.gap_gamma(lam, 40)
     L = int(np.ceil(1.5 * cnt))
-    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 2, it_max=30, precision=precision)
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 2, it_max=30, precision=precision, dense=dense)
     assert rc == 0 and nf == cnt
     tol = 1e-10 if precision == 0 else 1e-8
     assert np.all(np.abs(ev - lam[:cnt]) <= np.maximum(tol * lam[:cnt], 1e-9 * lam[0]))
