@@ -360,8 +360,84 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ld
   // *status is only ever raised (a failure of an earlier pass must survive).
 }
 
-void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st, const int *run_if) {
-  chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
+// The same factorisation with the k x k matrix held in shared memory (k^2 + k values of T):
+// L in the lower triangle, then X = L^{-1} computed row by row in place, X[i][c] (i > c)
+// stored at [c][i] and its diagonal in dX.  Row i of X:  X[i][c] = -(sum_{c <= l < i}
+// L[i][l] X[l][c]) / L[i][i].  With T = float it serves the first Cholesky-QR pass, whose
+// Gram matrix is only FP32-accurate anyway.
+template <typename T>
+__global__ void __launch_bounds__(1024) chol_inv_smem_kernel(int k, const double *__restrict__ G, int ldg,
+                                                             double *__restrict__ Rinv, int ldr, int *status,
+                                                             const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  T *A = reinterpret_cast<T *>(chol_smem);
+  T *dX = A + (size_t)k * k;
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e % k;
+    A[e] = j <= i ? (T)G[(size_t)i * ldg + j] : T(0);
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      const T d = A[j * k + j];
+      if (!(d > T(0)) || !isfinite((double)d)) fail = 1;
+      else A[j * k + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    const T piv = A[j * k + j];
+    for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] /= piv;
+    __syncthreads();
+    for (int i = j + 1 + warp; i < k; i += nw) {
+      const T lij = A[i * k + j];
+      for (int l = j + 1 + lane; l <= i; l += 32) A[i * k + l] -= lij * A[l * k + j];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) *status = SLRF_ECHOL;  // only ever raised
+    return;
+  }
+  for (int i = 0; i < k; ++i) {
+    for (int c = warp; c < i; c += nw) {
+      T sum = T(0);
+      for (int l = c + lane; l < i; l += 32) sum += A[i * k + l] * (l == c ? dX[c] : A[c * k + l]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) A[c * k + i] = -sum / A[i * k + i];
+    }
+    if (tid == 0) dX[i] = T(1) / A[i * k + i];
+    __syncthreads();
+  }
+  // Rinv[c][i] = X[i][c] (upper triangular)
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, i = e % k;
+    Rinv[(size_t)c * ldr + i] = i < c ? 0.0 : (double)(i == c ? dX[c] : A[c * k + i]);
+  }
+}
+
+constexpr size_t kCholSmemMax = 220 * 1024;
+
+void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st, const int *run_if,
+              bool fp32) {
+  static bool attrs = false;
+  if (!attrs) {
+    cudaFuncSetAttribute(chol_inv_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax);
+    cudaFuncSetAttribute(chol_inv_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax);
+    attrs = true;
+  }
+  const size_t b64 = ((size_t)k * k + k) * sizeof(double), b32 = ((size_t)k * k + k) * sizeof(float);
+  if (fp32 && b32 <= kCholSmemMax)
+    chol_inv_smem_kernel<float><<<1, 1024, b32, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
+  else if (b64 <= kCholSmemMax)
+    chol_inv_smem_kernel<double><<<1, 1024, b64, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
+  else
+    chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
 }
 
 // ------------------------------------------------------------------------------ Jacobi
@@ -663,41 +739,66 @@ void gaussian_block(int64_t n, int k, uint64_t seed, double *V, int ld, cudaStre
 // sigma_j = gamma x_j (1 + alpha i), x_j = (j - 1/2)/m; weights minimise
 // sum_t (Phi(t) - 1[t <= gamma])^2 + beta ||w/gamma||^2 on 3000 uniform samples of (0, 1]
 // and 3000 geometric samples of [band, 51] (normalised axis), via the normal equations.
-__global__ void design_poles_kernel(int m, int mp, double gamma, double alpha, double beta, double band,
-                                    double2 *sig, double2 *wt, int *status) {
+__global__ void __launch_bounds__(256) design_poles_kernel(int m, int mp, double gamma, double alpha, double beta,
+                                                           double band, double2 *sig, double2 *wt, int *status) {
   __shared__ double Nm[64][65];
   __shared__ double rhs[64];
   __shared__ double2 sh[32];
-  const int n2 = 2 * m;
+  constexpr int kCh = 16;            // samples per chunk
+  __shared__ double Gs[kCh][65];     // design rows of one chunk (+ target in column n2)
+  const int n2 = 2 * m, nc = n2 + 1;
   const int nin = 3000, nout = 3000;
   if (threadIdx.x < m) {
     const double x = (threadIdx.x + 0.5) / m;
     sh[threadIdx.x] = make_double2(x, alpha * x);
   }
-  __syncthreads();
-  // design matrix column a at sample t:  a < m: 2 Re C_a(t); a >= m: -2 Im C_{a-m}(t)
-  for (int e = threadIdx.x; e < n2 * (n2 + 1); e += blockDim.x) {
-    const int a = e / (n2 + 1), b = e % (n2 + 1);  // b == n2 -> right-hand side
-    double s = 0.0;
-    for (int t = 0; t < nin + nout; ++t) {
-      double tt, f;
-      if (t < nin) { tt = (t + 0.5) / nin; f = 1.0; }
-      else { tt = band * pow(51.0 / band, (double)(t - nin) / (nout - 1)); f = 0.0; }
-      const int ja = a < m ? a : a - m;
-      double dr = tt - sh[ja].x, di = -sh[ja].y;  // t - sigma
-      double den = dr * dr + di * di;
-      const double ga = a < m ? 2.0 * dr / den : -2.0 * (-di / den);
-      double gb;
-      if (b == n2) gb = f;
-      else {
-        const int jb = b < m ? b : b - m;
-        dr = tt - sh[jb].x; di = -sh[jb].y; den = dr * dr + di * di;
-        gb = b < m ? 2.0 * dr / den : -2.0 * (-di / den);
+  // design matrix column a at sample t:  a < m: 2 Re C_a(t); a >= m: -2 Im C_{a-m}(t); column
+  // n2 is the target (1 in the pass band, 0 in the stop band).  Each thread owns the entries
+  // e = threadIdx.x + 256 q of the n2 x (n2 + 1) normal equations and sums them over the
+  // samples in order.
+  double acc[17];
+#pragma unroll
+  for (int q = 0; q < 17; ++q) acc[q] = 0.0;
+  const int nent = n2 * nc;
+  for (int t0 = 0; t0 < nin + nout; t0 += kCh) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCh * nc; e += blockDim.x) {
+      const int tl = e / nc, a = e % nc, t = t0 + tl;
+      double v = 0.0;
+      if (t < nin + nout) {
+        double tt, f;
+        if (t < nin) { tt = (t + 0.5) / nin; f = 1.0; }
+        else { tt = band * pow(51.0 / band, (double)(t - nin) / (nout - 1)); f = 0.0; }
+        if (a == n2) v = f;
+        else {
+          const int ja = a < m ? a : a - m;
+          const double dr = tt - sh[ja].x, di = -sh[ja].y;  // t - sigma
+          const double den = dr * dr + di * di;
+          v = a < m ? 2.0 * dr / den : 2.0 * di / den;
+        }
       }
-      s = fma(ga, gb, s);
+      Gs[tl][a] = v;
     }
-    if (b == n2) rhs[a] = s;
-    else Nm[a][b] = s + (a == b ? beta : 0.0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 17; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < nent) {
+        const int a = e / nc, b = e % nc;
+        double s = acc[q];
+        for (int tl = 0; tl < kCh; ++tl) s = fma(Gs[tl][a], Gs[tl][b], s);
+        acc[q] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 17; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    if (e < nent) {
+      const int a = e / nc, b = e % nc;
+      if (b == n2) rhs[a] = acc[q];
+      else Nm[a][b] = acc[q] + (a == b ? beta : 0.0);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {

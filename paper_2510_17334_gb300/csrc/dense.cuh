@@ -29,9 +29,11 @@ void gemm_nn(int64_t n, const double *X, int ldx, int k1, const double *S, int l
              double alpha, double beta, bool upper, cudaStream_t st);
 
 // G = R^T R (lower Cholesky L = R^T of the symmetric k x k G, using its lower triangle);
-// Rinv (k x k row-major, upper) = R^{-1}.  *status = 0 or SLRF_ECHOL (device int).
+// Rinv (k x k row-major, upper) = R^{-1}.  *status is set to SLRF_ECHOL on failure and never
+// cleared (device int).  G may be overwritten.  fp32: factor in FP32 (first Cholesky-QR
+// pass).  In shared memory when k^2 values fit, else in global memory (FP64).
 void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st,
-              const int *run_if = nullptr);
+              const int *run_if = nullptr, bool fp32 = false);
 
 // Symmetric eigen-decomposition of H (k x k) by parallel cyclic Jacobi:
 // theta ascending (k), S (k x k row-major, column i = eigenvector i).

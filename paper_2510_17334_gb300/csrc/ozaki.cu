@@ -188,15 +188,30 @@ __device__ __forceinline__ void digits8(const double (&x)[8], int E, uint4 (&out
   for (int s = 0; s < kS; ++s) out[s] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
-// E[c] = max over rows of the exponent of X[r][c] (E pre-set to kESent bytes 0x80).
-__global__ void oz_colexp_kernel(int64_t n, const double *__restrict__ X, int ldx, int k, int *E,
-                                 const int *run_if) {
+// E[c] = max over rows of the exponent of X[r][c] (E pre-set to kESent bytes 0x80).  Block
+// 32 columns x 8 row lanes; a shared-memory max per block, then one atomicMax per column
+// (integer max: the result does not depend on the order).
+__global__ void __launch_bounds__(256) oz_colexp_kernel(int64_t n, const double *__restrict__ X, int ldx, int k,
+                                                        int *E, const int *run_if) {
   if (run_if != nullptr && *run_if == 0) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= k) return;
+  __shared__ int red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   int m = kESent;
-  for (int64_t r = blockIdx.y; r < n; r += gridDim.y) m = max(m, exp_of(X[r * ldx + c]));
-  if (m != kESent) atomicMax(E + c, m);
+  if (c < k)
+    for (int64_t r = (int64_t)blockIdx.y * 8 + threadIdx.y; r < n; r += (int64_t)gridDim.y * 8)
+      m = max(m, exp_of(X[r * ldx + c]));
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < k) {
+#pragma unroll
+    for (int y = 1; y < 8; ++y) m = max(m, red[y][threadIdx.x]);
+    if (m != kESent) atomicMax(E + c, m);
+  }
+}
+
+void colexp(int64_t n, const double *X, int ldx, int k, int *E, const int *run_if, cudaStream_t st) {
+  const int gy = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 1024);
+  oz_colexp_kernel<<<dim3((k + 31) / 32, gy), dim3(32, 8), 0, st>>>(n, X, ldx, k, E, run_if);
 }
 
 // Column operand: operand row i = column i of X, products over the rows of X.  One thread
@@ -538,12 +553,11 @@ void oz_gram(int64_t n, const double *X, int ldx, int k1, const double *Y, int l
   double *part = reinterpret_cast<double *>(w + lay.part_off);
   const int RA = (int)pad32(k1), RB = (int)pad32(k2);
   // exponents
-  const int ey = (int)std::min<int64_t>(std::max<int64_t>((n + 511) / 512, 1), 256);
   cudaMemsetAsync(EA, 0x80, sizeof(int) * RA, st);
-  oz_colexp_kernel<<<dim3((k1 + 127) / 128, ey), 128, 0, st>>>(n, X, ldx, k1, EA, run_if);
+  colexp(n, X, ldx, k1, EA, run_if, st);
   if (!same) {
     cudaMemsetAsync(EB, 0x80, sizeof(int) * RB, st);
-    oz_colexp_kernel<<<dim3((k2 + 127) / 128, ey), 128, 0, st>>>(n, Y, ldy, k2, EB, run_if);
+    colexp(n, Y, ldy, k2, EB, run_if, st);
   }
   // digits (the tail past the last k-block row groups stays as it is: only padded rows read it)
   {
@@ -592,8 +606,7 @@ void oz_gemm(int64_t n, const double *X, int ldx, int k1, const double *S, int l
   oz_split_rows_kernel<<<(unsigned)(RA / 8), 256, (size_t)kS * KB * 4 * 8 * sizeof(uint4), st>>>(
       n, X, ldx, k1, KB, (int)(RA / 8), dA, EA);
   cudaMemsetAsync(EB, 0x80, sizeof(int) * RB, st);
-  oz_colexp_kernel<<<dim3((k2 + 127) / 128, std::max(1, std::min(k1, 64))), 128, 0, st>>>(k1, S, lds, k2, EB,
-                                                                                           nullptr);
+  colexp(k1, S, lds, k2, EB, nullptr, st);
   {
     const int64_t tot = (int64_t)RB * KB * 4;
     oz_split_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k1, S, lds, k2, RB, KB, dB, EB, nullptr);

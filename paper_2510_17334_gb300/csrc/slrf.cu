@@ -477,7 +477,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st);
   cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
   tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, true);
-  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st);
+  chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st, nullptr, true);
   tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, false, ctx->iflags + 11);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st, ctx->iflags + 11);
   tsgemm(ctx, n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true);

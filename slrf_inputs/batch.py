@@ -60,31 +60,43 @@ def batch_gammas():
     return [(t["gamma"], t["count"]) for t in tab["problems"]]
 
 
-def _compute_gammas(P: int = 64, seed: int = 4):
+def _one_gamma(spec: BatchSpec):
     import scipy.sparse.linalg as spla
 
-    out = []
-    for spec in batch_specs(P, seed):
-        p = batch_pencil(spec)
-        A, B = p.A().tocsc(), p.B().tocsc()
-        k = spec.K + 6
-        # shift-invert at 0 with a symmetric minimum-degree ordering of A's factorisation
-        lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", options=dict(SymmetricMode=True))
-        opinv = spla.LinearOperator(A.shape, matvec=lu.solve, dtype=np.float64)
-        vals = spla.eigsh(A, k=k, M=B, sigma=0.0, which="LM", OPinv=opinv, return_eigenvectors=False, tol=1e-12)
-        lam = np.sort(vals)
-        # gap after the K-th eigenvalue, else the nearest clear gap
-        gaps = np.nonzero(np.diff(lam) > 1e-4 * lam[1:])[0]
-        g = gaps[np.argmin(np.abs(gaps + 1 - spec.K))]
-        out.append({"index": spec.index, "dim": spec.dim, "nodes": list(spec.nodes), "n": p.n, "nnz": p.nnz,
-                    "K": spec.K, "count": int(g + 1), "gamma": float(0.5 * (lam[g] + lam[g + 1])),
-                    "rel_gap": float((lam[g + 1] - lam[g]) / lam[g + 1]), "L": spec.L})
-        print(out[-1], flush=True)
+    p = batch_pencil(spec)
+    A, B = p.A().tocsc(), p.B().tocsc()
+    k = min(spec.K + 14, 74)
+    # shift-invert at 0 with a symmetric minimum-degree ordering of A's factorisation
+    lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", options=dict(SymmetricMode=True))
+    opinv = spla.LinearOperator(A.shape, matvec=lu.solve, dtype=np.float64)
+    vals = spla.eigsh(A, k=k, M=B, sigma=0.0, which="LM", OPinv=opinv, return_eigenvectors=False, tol=1e-12)
+    lam = np.sort(vals)
+    # gamma in the clear gap (>= 0.5 % of the upper eigenvalue) nearest to K eigenvalues, the
+    # count kept within 10..60
+    rel = np.diff(lam) / lam[1:]
+    cand = [g for g in range(9, min(len(lam) - 1, 60)) if rel[g] >= 5e-3]
+    if not cand:
+        cand = [int(np.argmax(rel[9:60])) + 9]
+    g = min(cand, key=lambda c: abs(c + 1 - spec.K))
+    return {"index": spec.index, "dim": spec.dim, "nodes": list(spec.nodes), "n": p.n, "nnz": p.nnz,
+            "K": spec.K, "count": int(g + 1), "gamma": float(0.5 * (lam[g] + lam[g + 1])),
+            "rel_gap": float(rel[g]), "L": spec.L, "lambda": [float(x) for x in lam]}
+
+
+def _compute_gammas(P: int = 64, seed: int = 4, workers: int = 6):
+    import multiprocessing as mp
+
+    specs = batch_specs(P, seed)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        out = pool.map(_one_gamma, specs, chunksize=1)
+    for o in out:
+        print({k: v for k, v in o.items() if k != "lambda"}, flush=True)
     return out
 
 
 if __name__ == "__main__":
     probs = _compute_gammas()
     with open(GAMMA_FILE, "w") as fh:
-        json.dump({"source": "scipy.sparse.linalg.eigsh shift-invert (sigma = 0, SuperLU MMD_AT_PLUS_A), tol 1e-12",
+        json.dump({"source": "scipy.sparse.linalg.eigsh shift-invert (sigma = 0, SuperLU MMD_AT_PLUS_A), tol 1e-12; "
+                             "gamma in the nearest gap of at least 0.5 %",
                    "problems": probs}, fh, indent=1)
