@@ -580,8 +580,31 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_init_kernel(con
   cocg_init_body<R>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(const CocgArgs<R> a) {
-  cocg_update_body<R, FIRST, FM>(a, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(const CocgArgs<R> a, int tile0) {
+  cocg_update_body<R, FIRST, FM>(a, blockIdx.x, tile0 + blockIdx.y);
+}
+// Two groups of tiles in one launch: the SpMM of tiles [s0, s0 + ns) and the update of tiles
+// [u0, u0 + nu).  Tiles are independent systems (own scalars, partial slots and counters),
+// so the two run side by side: the SpMM is bound by the FP64 pipe (or by the gather path
+// in FP32), the update by HBM.  Blocks alternate between the two kinds so that both are
+// resident from the start; within each kind the row block varies fastest.
+template <typename R, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(const CocgArgs<R> a, int s0, int ns,
+                                                                              int u0, int nu) {
+  const int NS = a.nrb * ns, NU = a.nrb * nu;
+  const int both = 2 * (NS < NU ? NS : NU);
+  const int b = blockIdx.x;
+  bool spmm;
+  int item;
+  if (b < both) {
+    spmm = (b & 1) == 0;
+    item = b >> 1;
+  } else {
+    spmm = NS > NU;
+    item = (b - both) + (NS < NU ? NS : NU);
+  }
+  if (spmm) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
+  else cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
 }
 template <typename R, bool FRESH>
 __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_kernel(const CocgArgs<R> a) {
@@ -699,9 +722,11 @@ template <typename R> static dim3 grid_of(const CocgArgs<R> &a) {
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
   cocg_init_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
 }
-template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st) {
-  const dim3 g = grid_of(a);
-#define UPD(F, M) cocg_update_kernel<R, F, M><<<g, kThreads, 0, st>>>(a)
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st, int tile0,
+                                      int ntiles) {
+  dim3 g = grid_of(a);
+  if (ntiles > 0) g.y = (unsigned)ntiles;
+#define UPD(F, M) cocg_update_kernel<R, F, M><<<g, kThreads, 0, st>>>(a, tile0)
   if (first) {
     switch (fm) {
       case kFinalNone: UPD(true, kFinalNone); break;
@@ -721,6 +746,22 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
   }
 #undef UPD
 }
+template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
+                                    cudaStream_t st) {
+  const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
+#define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
+  if (first) DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
+  else {
+    switch (fm) {
+      case kFinalNone: DUAL(false, kFinalNone); break;
+      case kFinalU: DUAL(false, kFinalU); break;
+      case kFinalStoreD: DUAL(false, kFinalStoreD); break;
+      case kFinalAddD: DUAL(false, kFinalAddD); break;
+      default: DUAL(false, kFinalUFromD); break;
+    }
+  }
+#undef DUAL
+}
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   if (fresh) cocg_spmm_kernel<R, true><<<grid_of(a), kThreads, 0, st>>>(a);
   else cocg_spmm_kernel<R, false><<<grid_of(a), kThreads, 0, st>>>(a);
@@ -731,8 +772,10 @@ template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st) 
 
 template void cocg_init<double>(const CocgArgs<double> &, cudaStream_t);
 template void cocg_init<float>(const CocgArgs<float> &, cudaStream_t);
-template void cocg_update<double>(const CocgArgs<double> &, bool, int, cudaStream_t);
-template void cocg_update<float>(const CocgArgs<float> &, bool, int, cudaStream_t);
+template void cocg_update<double>(const CocgArgs<double> &, bool, int, cudaStream_t, int, int);
+template void cocg_update<float>(const CocgArgs<float> &, bool, int, cudaStream_t, int, int);
+template void cocg_dual<double>(const CocgArgs<double> &, int, int, int, int, bool, int, cudaStream_t);
+template void cocg_dual<float>(const CocgArgs<float> &, int, int, int, int, bool, int, cudaStream_t);
 template void cocg_spmm<double>(const CocgArgs<double> &, cudaStream_t, bool);
 template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t, bool);
 template void cocg_residual<float>(const CocgArgs<float> &, cudaStream_t);

@@ -71,7 +71,12 @@ enum FinalMode { kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, 
 
 // Launchers (defined in cocg.cu).  All enqueue on `st`.
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);
-template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int final_mode, cudaStream_t st);
+// update of tiles [tile0, tile0 + ntiles) (ntiles = 0: every tile)
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int final_mode, cudaStream_t st,
+                                      int tile0 = 0, int ntiles = 0);
+// one launch: SpMM of tiles [s0, s0 + ns) and update of tiles [u0, u0 + nu)
+template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
+                                    cudaStream_t st);
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh = false);
 // refinement step s >= 2: r = r0 - (A - sigma B) D (FP64), new COCG scalars per w
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st);

@@ -166,3 +166,26 @@ def test_mixed_refinement_converges_to_the_fp64_filter(slrf_mod):
     assert errs[0] <= 1e-4
     assert errs[1] <= 1e-9 and errs[1] < errs[0]
     assert errs[2] <= 1e-12 and errs[2] <= errs[1]
+
+
+@pytest.mark.parametrize("precision,m", [(1, 8), (1, 16), (0, 8)])
+@pytest.mark.parametrize("warm", [False, True])
+def test_two_group_schedule_is_bitwise_sequential(slrf_mod, bar, precision, m, warm):
+    """The FP32 path's launch schedule splits the column tiles into two groups one launch
+    apart (each launch: SpMM of one group + update of the other).  Every tile performs the
+    same operations in the same order as in the kernel-by-kernel sequence of the timing
+    hook, so the two give bitwise equal filters and identical iteration counts.  13 columns:
+    FP32 tiles of 64 entries give 2 (m = 8) and 4 (m = 16) tiles; the FP64 path keeps the
+    sequential schedule and is checked the same way."""
+    p, lam, gamma = bar
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L,
+                           slrf_mod.slrf_opts_default(m=m, it_max=25, precision=precision))
+    V1 = torch.from_numpy(si.start_block(N, L, 7))
+    th = torch.from_numpy(np.linspace(0.2, 1.4, L) * gamma) if warm else None
+    U = ctx.filter_apply(V1, th).cpu().numpy()
+    its, rr, _ = ctx.filter_stats(L)
+    tm = ctx.filter_timing(V1, th)
+    its2, rr2, _ = ctx.filter_stats(L)
+    assert np.array_equal(U, tm["U"].cpu().numpy())
+    assert np.array_equal(its, its2) and np.array_equal(rr, rr2)
+    ctx.close()
