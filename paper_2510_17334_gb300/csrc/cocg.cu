@@ -29,6 +29,12 @@
 #ifndef SLRF_SPMM_PREFETCH
 #define SLRF_SPMM_PREFETCH 0
 #endif
+#ifndef SLRF_GATHER_UNROLL
+#define SLRF_GATHER_UNROLL 8
+#endif
+namespace slrf {
+constexpr int kGatherUnroll = SLRF_GATHER_UNROLL;  // CSR entries of a row in flight per warp
+}
 
 namespace slrf {
 
@@ -378,7 +384,7 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
         int cl = 0;
         R avl = 0, bvl = 0;
         if (lane < cnt) { cl = a.col[e0 + lane]; avl = a.valA[e0 + lane]; bvl = a.valB[e0 + lane]; }
-#pragma unroll 4
+#pragma unroll kGatherUnroll
         for (int t = 0; t < cnt; ++t) {
           const int c = __shfl_sync(0xffffffffu, cl, t);
           const R av = __shfl_sync(0xffffffffu, avl, t);
