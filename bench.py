@@ -169,6 +169,8 @@ def main():
                     help="batch64: also time the plain FP64 batched solve")
     ap.add_argument("--mixed-it-max", type=int, default=15,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
+    ap.add_argument("--directions", type=int, default=8,
+                    help="sens48: random directions of the finite-difference check")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -179,6 +181,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "batch64":
         return batch_bench(args, rank, world, local)
+    if args.workload == "sens48":
+        return sens_bench(args, rank, world, local)
 
     import numpy as np
     import torch
@@ -400,6 +404,104 @@ def batch_bench(args, rank, world, local):
                                     f"one persistent COCG launch per phase"),
                        "precision": "mixed (complex-FP32 COCG, FP64 outer)", "autotune": 1},
             "batched_mixed": main, "batched_fp64": fp64, "gpu_launches": main["kernel_launches"], "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def sens_bench(args, rank, world, local):
+    """Eigenvalue sensitivity of the 48^3 Q1 elasticity box: lowest 50 eigenpairs (mixed
+    path), loss L = sum_i c_i lambda_i, c ~ N(0, 1), and its gradient with respect to the
+    per-element stiffness parameters p_e through the eigenvalue adjoint (slrf_eig_grad).
+    A = sum_e p_e K_e is linear in p, so for a direction dp the directional derivative is
+    <gA, values of A assembled with p = dp> (B does not depend on p).  It is checked against
+    the closed form sum_i c_i x_i^T dA x_i and against central differences of L at
+    p +- h dp (h = 1e-6, relative directions dp = p .* N(0, 1)), each a warm-started solve."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+
+    ge.build()
+    from slrf_inputs import elastic as se
+    from paper_2510_17334_gb300 import slrf
+
+    name = "elast_48"
+    spec = se.SPECS[name]
+    pe = se.element_params(name)
+    P0 = se.pencil(name, pe)
+    gamma, cnt = se.gamma(name)
+    L = spec["block"]
+    rng = np.random.default_rng(11)
+    cvec = rng.standard_normal(cnt)
+    it = args.it_max or 20
+    opts = slrf.slrf_opts_default(it_max=it, precision=1, tol_eig=1e-9)
+    V0 = torch.from_numpy(__import__("slrf_inputs").start_block(P0.n, L, spec["seed"])).cuda()
+
+    def solve(valA, V):
+        ctx = slrf.Context(P0.rowptr, P0.col, valA, P0.valB, gamma, L, opts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, nf, ev, X, rs, st = ctx.solve(V, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return ctx, rc, nf, ev, X, rs, st, e0.elapsed_time(e1)
+
+    cp, cf = clocks_start()
+    ctx, rc, nf, ev, X, rs, st, ms_solve = solve(P0.valA, V0)
+    assert rc == 0 and nf == cnt, (rc, nf, cnt)
+    cd = torch.from_numpy(cvec).cuda()
+    ctx.eig_grad(ev, X, cd)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gA, gB = ctx.eig_grad(ev, X, cd)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1)
+    ctx.close()
+    Xh = X.cpu().numpy()
+    evh = ev.cpu().numpy()
+    gAh = gA.cpu().numpy()
+    L0 = float(cvec @ evh)
+    # warm start of the perturbed solves: the eigenvectors plus Gaussian columns
+    Vw = V0.clone()
+    Vw[:, :cnt] = X
+    A0 = P0.A().tocsr()
+    h = 1e-6
+    err_cf, err_fd, rows = [], [], []
+    for d in range(args.directions):
+        dp = pe * rng.standard_normal(pe.size)
+        dP = se.pencil(name, dp)
+        assert np.array_equal(dP.rowptr, P0.rowptr) and np.array_equal(dP.col, P0.col)
+        g_adj = float(gAh @ dP.valA)
+        dA = dP.A().tocsr()
+        g_cf = float(np.sum(cvec * np.einsum("ij,ij->j", Xh, dA @ Xh)))
+        Ls = []
+        for sgn in (1.0, -1.0):
+            c2, rc2, nf2, ev2, X2, rs2, st2, _ = solve(P0.valA + sgn * h * dP.valA, Vw)
+            c2.close()
+            assert rc2 == 0 and nf2 == cnt, (rc2, nf2)
+            Ls.append(float(cvec @ ev2.cpu().numpy()))
+        g_fd = (Ls[0] - Ls[1]) / (2 * h)
+        err_cf.append(abs(g_adj - g_cf) / abs(g_cf))
+        err_fd.append(abs(g_adj - g_fd) / abs(g_fd))
+        rows.append({"adjoint": g_adj, "closed_form": g_cf, "central_fd": g_fd})
+    clk = clocks_stop(cp, cf, local)
+    line = {"metric": "eigenvalue-sensitivity gradient dL/dp vs closed form and central differences",
+            "value": max(err_fd) if err_fd else None, "unit": "max relative error (central FD)",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f64 (adjoint), c32-in-f64 (solve)",
+            "config": {"workload": (f"sens48: 3D Q1 elasticity 48^3 nodes, z=0 clamped (n={P0.n}, nnz={P0.nnz}), "
+                                    f"p_e lognormal(0,0.5) seed {spec['seed']}, lowest {cnt} eigenpairs, block {L}, "
+                                    f"L = sum c_i lambda_i, c ~ N(0,1) seed 11"),
+                       "it_max": it, "h": h, "directions": args.directions},
+            "solve": {"ms": ms_solve, "eigenpairs": nf, "max_resid": float(rs.max().item()),
+                      "outer_iters": st["outer_iters"], "loss": L0},
+            "adjoint": {"ms": ms_adj, "nnz": P0.nnz, "eigenpairs": cnt,
+                        "gbs_algorithmic": (P0.nnz * (8 + 8 + 12) + P0.n * cnt * 8) / (ms_adj * 1e6)},
+            "max_rel_err_vs_closed_form": max(err_cf) if err_cf else None,
+            "max_rel_err_vs_central_fd": max(err_fd) if err_fd else None,
+            "directions_detail": rows, "clocks": clk}
     if rank == 0:
         print(json.dumps(line))
 

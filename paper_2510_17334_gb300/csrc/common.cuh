@@ -94,9 +94,11 @@ __device__ inline bool grid_sync(const GridBarrier &gb, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*vgen == g) {
-        if (*(volatile int *)gb.err) { ok = 0; break; }
-        if (++spins > (1ll << 22)) { atomicExch(gb.err, 1); ok = 0; break; }
-        __nanosleep(64);
+        if ((++spins & 63) == 0) {
+          if (*(volatile int *)gb.err) { ok = 0; break; }
+          if (spins > (1ll << 22)) { atomicExch(gb.err, 1); ok = 0; break; }  // a few seconds of polls
+          __nanosleep(32);
+        }
       }
     }
     __threadfence();

@@ -479,12 +479,12 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
   __shared__ double cs[512][2];        // rotation (c, s) of every index for this round
   __shared__ double red[128];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // largest |a_pq| / sqrt(|a_pp a_qq|) met this sweep; identical in every block
-    double off_max = 0.0;
+    // largest |a_pq| / sqrt(|a_pp a_qq|) met this sweep (per thread, reduced once per sweep;
+    // identical in every block since every block computes every rotation)
+    double my_off = 0.0;
     for (int r = 0; r < kk - 1; ++r) {
       // every block computes every rotation of the round (kk/2 independent 2x2 problems),
       // so no barrier is needed between the rotation and the update phase
-      double my_off = 0.0;
       for (int b = threadIdx.x; b < kk / 2; b += blockDim.x) {
         int p, q;
         rr_pair(kk, r, b, p, q);
@@ -503,23 +503,20 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
         cs[p][0] = c; cs[p][1] = sn;
         cs[q][0] = c; cs[q][1] = sn;
       }
-      red[threadIdx.x] = my_off;
-      __syncthreads();
-      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-      }
-      off_max = fmax(off_max, red[0]);
       for (int b = blockIdx.x; b < kk / 2; b += nb) {
         int p, q;
         rr_pair(kk, r, b, p, q);
-        const double c = cs[p][0], sn = cs[p][1];
-        for (int x = threadIdx.x; x < kk; x += blockDim.x) {
+        // rows p, q of A and of V^T, fetched together (kk <= 512: at most 4 per thread)
+        double vpr[4], vqr[4];
+        for (int x = threadIdx.x, u = 0; x < kk; x += blockDim.x, ++u) {
           rp[x] = __ldcg(&A[(size_t)p * kk + x]);
           rq[x] = __ldcg(&A[(size_t)q * kk + x]);
+          vpr[u] = __ldcg(&Vt[(size_t)p * kk + x]);
+          vqr[u] = __ldcg(&Vt[(size_t)q * kk + x]);
         }
         __syncthreads();
-        for (int x = threadIdx.x; x < kk; x += blockDim.x) {
+        const double c = cs[p][0], sn = cs[p][1];
+        for (int x = threadIdx.x, u = 0; x < kk; x += blockDim.x, ++u) {
           const int y = rr_partner(kk, r, x);
           const double c2 = cs[x][0], s2 = cs[x][1];
           const bool first = x < y;  // the smaller index is p of its pair
@@ -532,14 +529,21 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
           if (x == p) nq = 0.0;
           A[(size_t)p * kk + x] = np;
           A[(size_t)q * kk + x] = nq;
-          const double vp = __ldcg(&Vt[(size_t)p * kk + x]), vq = __ldcg(&Vt[(size_t)q * kk + x]);
-          Vt[(size_t)p * kk + x] = c * vp - sn * vq;
-          Vt[(size_t)q * kk + x] = sn * vp + c * vq;
+          Vt[(size_t)p * kk + x] = c * vpr[u] - sn * vqr[u];
+          Vt[(size_t)q * kk + x] = sn * vpr[u] + c * vqr[u];
         }
         __syncthreads();
       }
       if (!grid_sync(gb, nb)) return;
     }
+    red[threadIdx.x] = my_off;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    const double off_max = red[0];
+    __syncthreads();
     // quadratic convergence: once every off-diagonal met in a sweep is below 1e-8 of its
     // diagonal scale, the rotations of that sweep leave them at rounding level
     if (off_max < 1e-8) break;
