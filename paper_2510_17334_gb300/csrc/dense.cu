@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
                                                         const double *__restrict__ valB,
                                                         const double *__restrict__ X, int ldx, int k,
                                                         double *__restrict__ YA, double *__restrict__ YB,
-                                                        int ldy) {
+                                                        int ldy, const int *run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -59,10 +60,58 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
 }
 
 void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
-               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st) {
+               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st,
+               const int *run_if) {
   if (n <= 0 || k <= 0) return;
   dim3 grid((unsigned)((n + 7) / 8), (unsigned)((k + 127) / 128));
-  spmm_real_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy);
+  spmm_real_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy, run_if);
+}
+
+// YB = B X with FP32 products and sums (FP64 in and out): for the first Cholesky-QR pass,
+// whose Gram matrix is formed in FP32 anyway.  Same work split as spmm_real_kernel.
+__global__ void __launch_bounds__(256) spmm_b32_kernel(int64_t n, const int64_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ col,
+                                                       const double *__restrict__ valB,
+                                                       const double *__restrict__ X, int ldx, int k,
+                                                       double *__restrict__ YB, int ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int c0 = blockIdx.y * 128 + lane;
+  float sb[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t rs = rowptr[i], re = rowptr[i + 1];
+  for (int64_t e0 = rs; e0 < re; e0 += 32) {
+    const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
+    int cl = 0;
+    float bl = 0.f;
+    if (lane < cnt) {
+      cl = col[e0 + lane];
+      bl = (float)valB[e0 + lane];
+    }
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) {
+      const int c = __shfl_sync(0xffffffffu, cl, t);
+      const float b = __shfl_sync(0xffffffffu, bl, t);
+      const double *xr = X + (size_t)c * ldx;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cc = c0 + 32 * u;
+        if (cc < k) sb[u] = fmaf(b, (float)xr[cc], sb[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int cc = c0 + 32 * u;
+    if (cc < k) YB[(size_t)i * ldy + cc] = (double)sb[u];
+  }
+}
+
+void spmm_b32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valB, const double *X, int ldx,
+              int k, double *YB, int ldy, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return;
+  dim3 grid((unsigned)((n + 7) / 8), (unsigned)((k + 127) / 128));
+  spmm_b32_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valB, X, ldx, k, YB, ldy);
 }
 
 __global__ void shifted_residual_kernel(int64_t n, int k, const double *AV, const double *BV, int ld,
@@ -360,9 +409,9 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, double *G, int ld
   // *status is only ever raised (a failure of an earlier pass must survive).
 }
 
-// The same factorisation with the k x k matrix held in shared memory (k^2 + k values of T):
+// The same factorisation with the k x k matrix held in shared memory (k^2 + 3k values of T):
 // L in the lower triangle, then X = L^{-1} computed row by row in place, X[i][c] (i > c)
-// stored at [c][i] and its diagonal in dX.  Row i of X:  X[i][c] = -(sum_{c <= l < i}
+// stored at [c][i] and its diagonal 1/L[i][i] in pvi.  Row i of X:  X[i][c] = -(sum_{c <= l < i}
 // L[i][l] X[l][c]) / L[i][i].  With T = float it serves the first Cholesky-QR pass, whose
 // Gram matrix is only FP32-accurate anyway.
 template <typename T>
@@ -372,7 +421,10 @@ __global__ void __launch_bounds__(1024) chol_inv_smem_kernel(int k, const double
   if (run_if != nullptr && *run_if == 0) return;
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T *A = reinterpret_cast<T *>(chol_smem);
-  T *dX = A + (size_t)k * k;
+  T *colj = A + (size_t)k * k;  // column j of L, contiguous (rows of A are k apart: a column
+                                // read by consecutive lanes would hit one shared-memory bank)
+  T *pv = colj + k;             // pivots L[j][j]
+  T *pvi = pv + k;              // 1 / L[j][j] (= X[j][j])
   __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -380,22 +432,33 @@ __global__ void __launch_bounds__(1024) chol_inv_smem_kernel(int k, const double
     const int i = e / k, j = e % k;
     A[e] = j <= i ? (T)G[(size_t)i * ldg + j] : T(0);
   }
+  // each pivot's square root and reciprocal are taken once, by the thread whose update
+  // produced it (FP64 sqrt and division are many FP64-pipe operations on this GPU)
+  auto take_pivot = [&](int j, T d) {
+    if (!(d > T(0)) || !isfinite((double)d)) fail = 1;
+    else { const T r = sqrt(d); pv[j] = r; pvi[j] = T(1) / r; }
+  };
   if (tid == 0) fail = 0;
   __syncthreads();
+  if (tid == 0) take_pivot(0, A[0]);
+  __syncthreads();
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      const T d = A[j * k + j];
-      if (!(d > T(0)) || !isfinite((double)d)) fail = 1;
-      else A[j * k + j] = sqrt(d);
+    if (fail) break;
+    const T ip = pvi[j];
+    for (int i = j + 1 + tid; i < k; i += nt) {
+      const T lij = A[i * k + j] * ip;
+      A[i * k + j] = lij;
+      colj[i] = lij;
     }
     __syncthreads();
-    if (fail) break;
-    const T piv = A[j * k + j];
-    for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] /= piv;
-    __syncthreads();
+    if (tid == 0) A[j * k + j] = pv[j];
     for (int i = j + 1 + warp; i < k; i += nw) {
-      const T lij = A[i * k + j];
-      for (int l = j + 1 + lane; l <= i; l += 32) A[i * k + l] -= lij * A[l * k + j];
+      const T lij = colj[i];
+      for (int l = j + 1 + lane; l <= i; l += 32) {
+        const T v = A[i * k + l] - lij * colj[l];
+        A[i * k + l] = v;
+        if (i == j + 1 && l == j + 1) take_pivot(j + 1, v);
+      }
     }
     __syncthreads();
   }
@@ -403,21 +466,21 @@ __global__ void __launch_bounds__(1024) chol_inv_smem_kernel(int k, const double
     if (tid == 0) *status = SLRF_ECHOL;  // only ever raised
     return;
   }
-  for (int i = 0; i < k; ++i) {
+  // X = L^{-1} row by row: X[i][c] = -(sum_{c <= l < i} L[i][l] X[l][c]) / L[i][i], stored at [c][i]
+  for (int i = 1; i < k; ++i) {
     for (int c = warp; c < i; c += nw) {
       T sum = T(0);
-      for (int l = c + lane; l < i; l += 32) sum += A[i * k + l] * (l == c ? dX[c] : A[c * k + l]);
+      for (int l = c + lane; l < i; l += 32) sum += A[i * k + l] * (l == c ? pvi[c] : A[c * k + l]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane == 0) A[c * k + i] = -sum / A[i * k + i];
+      if (lane == 0) A[c * k + i] = -sum * pvi[i];
     }
-    if (tid == 0) dX[i] = T(1) / A[i * k + i];
     __syncthreads();
   }
   // Rinv[c][i] = X[i][c] (upper triangular)
   for (int e = tid; e < k * k; e += nt) {
     const int c = e / k, i = e % k;
-    Rinv[(size_t)c * ldr + i] = i < c ? 0.0 : (double)(i == c ? dX[c] : A[c * k + i]);
+    Rinv[(size_t)c * ldr + i] = i < c ? 0.0 : (double)(i == c ? pvi[c] : A[c * k + i]);
   }
 }
 
@@ -431,7 +494,7 @@ void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cud
     cudaFuncSetAttribute(chol_inv_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax);
     attrs = true;
   }
-  const size_t b64 = ((size_t)k * k + k) * sizeof(double), b32 = ((size_t)k * k + k) * sizeof(float);
+  const size_t b64 = ((size_t)k * k + 3 * k) * sizeof(double), b32 = ((size_t)k * k + 3 * k) * sizeof(float);
   if (fp32 && b32 <= kCholSmemMax)
     chol_inv_smem_kernel<float><<<1, 1024, b32, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
   else if (b64 <= kCholSmemMax)

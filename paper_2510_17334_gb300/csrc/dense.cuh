@@ -9,7 +9,10 @@ namespace slrf {
 // YA = A X and/or YB = B X for a real row-major block X (n x k).  Either output may be null.
 void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA,
                const double *valB, const double *X, int ldx, int k, double *YA, double *YB, int ldy,
-               cudaStream_t st);
+               cudaStream_t st, const int *run_if = nullptr);
+// YB = B X in FP32 arithmetic (FP64 storage): input of an FP32 Gram matrix.
+void spmm_b32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valB, const double *X, int ldx,
+              int k, double *YB, int ldy, cudaStream_t st);
 
 // R = AV - theta .* BV (column-wise theta), row-major n x k.
 void shifted_residual(int64_t n, int k, const double *AV, const double *BV, int ld, const double *theta,

@@ -7,7 +7,8 @@
 // 1 KB: the MMA kernel fetches them with plain bulk copies and reads them through
 // no-swizzle shared-memory descriptors (core matrix stride 128 B along K, 256 B along rows).
 //
-// MMA kernel.  One CTA computes a 128 x 32 output tile over a range of k-blocks:
+// MMA kernel.  A work unit is a 128 x 32 output tile over a range of k-blocks; CTAs are
+// persistent (one per SM) and walk the units b, b + gridDim.x, ...:
 //   warp 4 lane 0   bulk-copies 7 A and 7 B slices per k-block into a 3-stage ring;
 //   warp 5          allocates TMEM; lane 0 issues 2 x 28 MMAs (M128 N32 K16) per k-block
 //                   into six accumulators (levels 0..4 and the merged 5..6) of one of two
@@ -281,6 +282,7 @@ struct OzMma {
   int kb_per_split;
   int m_tiles, n_tiles;
   int sym;
+  int tiles, units;  // output tiles; work units = tiles x row splits
   int mode;          // 0: FP64 partial tiles to part; 1: Z = alpha 2^(EA+EB-16) D + beta Z
   double *part;
   int MR, NC;        // partial tile array: [split][MR][NC]
@@ -305,6 +307,19 @@ __device__ __forceinline__ void tile_of(const OzMma &p, int idx, int &t, int &u)
   t = 0; u = 0;
 }
 
+// Work unit q: tile (q mod tiles) over the k-blocks of row split (q / tiles).  Consecutive
+// units share their row split (Gram) or their 128-row tile of A (product), so the CTAs in
+// flight re-read the same digit tiles from L2.
+__device__ __forceinline__ void unit_of(const OzMma &p, int q, int &t, int &u, int &split, int &kb0, int &nkb) {
+  split = q / p.tiles;
+  tile_of(p, q % p.tiles, t, u);
+  kb0 = split * p.kb_per_split;
+  nkb = min(p.KB, kb0 + p.kb_per_split) - kb0;  // >= 1 by construction
+}
+
+// Persistent: CTA b takes the units b, b + gridDim.x, ...; the three roles walk the same
+// sequence, so the copy ring, the MMA stream and the TMEM double buffer run on across
+// unit boundaries (k-block counter g, chunk counter c).
 __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
   if (p.run_if != nullptr && *p.run_if == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -312,12 +327,6 @@ __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
   uint64_t *full = bars, *empty = bars + 3, *tfull = bars + 6, *tempty = bars + 8, *done = bars + 10;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 11);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int t, u;
-  tile_of(p, blockIdx.x, t, u);
-  const int split = blockIdx.y;
-  const int kb0 = split * p.kb_per_split;
-  const int kb1 = min(p.KB, kb0 + p.kb_per_split);
-  const int nkb = kb1 - kb0;  // >= 1 by construction of the grid
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) { mbar_init(full + i, 1); mbar_init(empty + i, 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, 128); }
@@ -332,52 +341,67 @@ __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
 
   if (warp == 4) {
     if (lane == 0) {
-      int issued = 0;
-      for (int i = 0; i < nkb; ++i) {
-        const int s_ = i % kStages;
-        if (i >= kStages && !mbar_wait(empty + s_, ((i / kStages) - 1) & 1, p.err, 1)) break;
-        unsigned char *sa = smem + s_ * kStage, *sb = sa + kStageA;
-        mbar_expect_tx(full + s_, kStage);
-        const int kb = kb0 + i;
+      int g = 0;
+      bool ok = true;
+      for (int q = blockIdx.x; q < p.units && ok; q += gridDim.x) {
+        int t, u, split, kb0, nkb;
+        unit_of(p, q, t, u, split, kb0, nkb);
+        for (int i = 0; i < nkb; ++i, ++g) {
+          const int s_ = g % kStages;
+          if (g >= kStages && !mbar_wait(empty + s_, ((g / kStages) - 1) & 1, p.err, 1)) { ok = false; break; }
+          unsigned char *sa = smem + s_ * kStage, *sb = sa + kStageA;
+          mbar_expect_tx(full + s_, kStage);
+          const int kb = kb0 + i;
 #pragma unroll 1
-        for (int sl = 0; sl < kS; ++sl)
+          for (int sl = 0; sl < kS; ++sl)
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            bulk_g2s(sa + (sl * 2 + j) * kATile, p.dA + off16(sl, p.KB, kb, j, p.RA8, 16 * t, 0, 0) * 8, kATile,
-                     full + s_);
-            bulk_g2s(sb + (sl * 2 + j) * kBTile, p.dB + off16(sl, p.KB, kb, j, p.RB8, 4 * u, 0, 0) * 8, kBTile,
-                     full + s_);
-          }
-        issued = i + 1;
+            for (int j = 0; j < 2; ++j) {
+              bulk_g2s(sa + (sl * 2 + j) * kATile, p.dA + off16(sl, p.KB, kb, j, p.RA8, 16 * t, 0, 0) * 8, kATile,
+                       full + s_);
+              bulk_g2s(sb + (sl * 2 + j) * kBTile, p.dB + off16(sl, p.KB, kb, j, p.RB8, 4 * u, 0, 0) * 8, kBTile,
+                       full + s_);
+            }
+        }
       }
       // every armed stage has landed before the CTA may exit (a no-op in normal runs)
-      for (int i = max(0, issued - kStages); i < issued; ++i) mbar_wait(full + i % kStages, (i / kStages) & 1, p.err, 6);
+      for (int i = max(0, g - kStages); i < g; ++i) mbar_wait(full + i % kStages, (i / kStages) & 1, p.err, 6);
     }
   } else if (warp == 5) {
     if (lane == 0) {
       const uint32_t sbase = su32(smem);
-      for (int i = 0; i < nkb; ++i) {
-        const int c = i / kChunkKB, buf = c & 1;
-        const bool first = (i % kChunkKB) == 0;
-        if (first && c >= 2 && !mbar_wait(tempty + buf, ((c >> 1) - 1) & 1, p.err, 2)) break;
-        const int s_ = i % kStages;
-        if (!mbar_wait(full + s_, (i / kStages) & 1, p.err, 3)) break;
-        tc_fence_after();
-        const uint32_t a0 = sbase + s_ * kStage, b0 = a0 + kStageA;
-        const uint32_t dbuf = tmem + (uint32_t)(buf * kAcc * kTN);
+      int g = 0, c = 0, buf = 0;
+      bool ok = true;
+      for (int q = blockIdx.x; q < p.units && ok; q += gridDim.x) {
+        int t, u, split, kb0, nkb;
+        unit_of(p, q, t, u, split, kb0, nkb);
+        for (int i = 0; i < nkb; ++i, ++g) {
+          const bool first = (i % kChunkKB) == 0;
+          if (first) {
+            buf = c & 1;
+            if (c >= 2 && !mbar_wait(tempty + buf, ((c >> 1) - 1) & 1, p.err, 2)) { ok = false; break; }
+          }
+          const int s_ = g % kStages;
+          if (!mbar_wait(full + s_, (g / kStages) & 1, p.err, 3)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = sbase + s_ * kStage, b0 = a0 + kStageA;
+          const uint32_t dbuf = tmem + (uint32_t)(buf * kAcc * kTN);
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+          for (int j = 0; j < 2; ++j)
 #pragma unroll
-          for (int sl = 0; sl < kS; ++sl)
+            for (int sl = 0; sl < kS; ++sl)
 #pragma unroll
-            for (int tl = 0; tl + sl < kS; ++tl) {
-              const int lvl = sl + tl < 5 ? sl + tl : 5;
-              const uint32_t acc = (first && j == 0 && sl == 0 && tl <= 5) ? 0u : 1u;
-              mma_bf16(dbuf + (uint32_t)(lvl * kTN), sdesc(a0 + (sl * 2 + j) * kATile),
-                       sdesc(b0 + (tl * 2 + j) * kBTile), kIdesc, acc);
-            }
-        mma_commit(empty + s_);
-        if ((i % kChunkKB) == kChunkKB - 1 || i == nkb - 1) mma_commit(tfull + buf);
+              for (int tl = 0; tl + sl < kS; ++tl) {
+                const int lvl = sl + tl < 5 ? sl + tl : 5;
+                const uint32_t acc = (first && j == 0 && sl == 0 && tl <= 5) ? 0u : 1u;
+                mma_bf16(dbuf + (uint32_t)(lvl * kTN), sdesc(a0 + (sl * 2 + j) * kATile),
+                         sdesc(b0 + (tl * 2 + j) * kBTile), kIdesc, acc);
+              }
+          mma_commit(empty + s_);
+          if ((i % kChunkKB) == kChunkKB - 1 || i == nkb - 1) {
+            mma_commit(tfull + buf);
+            ++c;
+          }
+        }
       }
       mma_commit(done);
       mbar_wait(done, 0, p.err, 4);
@@ -385,48 +409,69 @@ __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
     __syncwarp();
   } else {
     // epilogue: warp w owns TMEM lanes 32w..32w+31 = output rows 128t + 32w + lane
-    long long I[32];
-    float f5[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) { I[q] = 0; f5[q] = 0.f; }
-    const int nch = (nkb + kChunkKB - 1) / kChunkKB;
+    int c = 0;
     bool ok = true;
-    for (int c = 0; c < nch && ok; ++c) {
-      const int buf = c & 1;
-      if (!mbar_wait(tfull + buf, (c >> 1) & 1, p.err, 5)) { ok = false; break; }
-      tc_fence_after();
-      const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kAcc * kTN);
-      float v[32];
+    for (int q = blockIdx.x; q < p.units && ok; q += gridDim.x) {
+      int t, u, split, kb0, nkb;
+      unit_of(p, q, t, u, split, kb0, nkb);
+      long long I[32];
+      float f5[32];
 #pragma unroll
-      for (int lvl = 0; lvl < 5; ++lvl) {
-        tmem_ld32(tb + (uint32_t)(lvl * kTN), v);
-        const float sc = __int_as_float((127 + 8 * lvl) << 23);  // 2^(8 lvl)
+      for (int qq = 0; qq < 32; ++qq) { I[qq] = 0; f5[qq] = 0.f; }
+      const int nch = (nkb + kChunkKB - 1) / kChunkKB;
+      for (int k = 0; k < nch; ++k, ++c) {
+        const int buf = c & 1;
+        if (!mbar_wait(tfull + buf, (c >> 1) & 1, p.err, 5)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kAcc * kTN);
+        float v[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) I[q] += (long long)__float2int_rn(v[q] * sc) << (8 * (4 - lvl));
+        for (int lvl = 0; lvl < 5; ++lvl) {
+          tmem_ld32(tb + (uint32_t)(lvl * kTN), v);
+          const float sc = __int_as_float((127 + 8 * lvl) << 23);  // 2^(8 lvl)
+#pragma unroll
+          for (int qq = 0; qq < 32; ++qq)
+            I[qq] += (long long)__float2int_rn(v[qq] * sc) * (1ll << (8 * (4 - lvl)));
+        }
+        tmem_ld32(tb + (uint32_t)(5 * kTN), v);
+#pragma unroll
+        for (int qq = 0; qq < 32; ++qq) f5[qq] += v[qq];
+        tc_fence_before();
+        mbar_arrive(tempty + buf);
       }
-      tmem_ld32(tb + (uint32_t)(5 * kTN), v);
+      if (!ok) break;
+      // Sum of the levels in FP64 (the merged levels keep their FP32 sum's bits: rounding
+      // them into the 64-bit units would cost 2^-49 of a single product); powers of two are
+      // applied to the exponent bits.  GB300 runs FP64 at 2 operations per clock per SM, so
+      // the finish of 128 x 32 outputs per unit is kept to three FP64 operations each.
+      const int64_t row = (int64_t)kTM * t + 32 * warp + lane;
+      if (p.mode == 0) {
+        double *dst = p.part + ((int64_t)split * p.MR + row) * p.NC + kTN * u;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) f5[q] += v[q];
-      tc_fence_before();
-      mbar_arrive(tempty + buf);
-    }
-    const int64_t row = (int64_t)kTM * t + 32 * warp + lane;
-    if (p.mode == 0) {
-      double *dst = p.part + ((int64_t)split * p.MR + row) * p.NC + kTN * u;
+        for (int qq = 0; qq < 32; ++qq) dst[qq] = fma((double)I[qq], 0x1p-32, (double)f5[qq]);
+      } else if (row < p.rows) {
+        const int ea = max(p.EA[row], -1100);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) dst[q] = (double)I[q] * 0x1p-32 + (double)f5[q];
-    } else if (row < p.rows) {
-      const int ea = max(p.EA[row], -1100);
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int col = kTN * u + q;
-        if (col >= p.cols) continue;
-        const int eb = max(p.EB[col], -1100);
-        double z = (double)I[q] * 0x1p-32 + (double)f5[q];
-        z = (ea == kENonFinite || eb == kENonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                     : scalbn(z, ea + eb - 16);
-        double *zp = p.Z + row * p.ldz + col;
-        *zp = (p.beta == 0.0) ? p.alpha * z : fma(p.alpha, z, p.beta * *zp);
+        for (int qq = 0; qq < 32; ++qq) {
+          const int col = kTN * u + qq;
+          if (col >= p.cols) continue;
+          const int eb = max(p.EB[col], -1100);
+          double z = fma((double)f5[qq], 4294967296.0, (double)I[qq]);  // in units of 2^-32
+          const int e = ea + eb - 48;  // value = z 2^(EA + EB - 16 - 32)
+          if (ea == kENonFinite || eb == kENonFinite) {
+            z = __longlong_as_double(0x7ff8000000000000ll);
+          } else if (z != 0.0) {
+            const int ez = (int)((__double_as_longlong(z) >> 52) & 0x7FF);  // biased exponent of z (>= 1023)
+            if (ez + e >= 1 && ez + e <= 2046) z = __longlong_as_double(__double_as_longlong(z) + ((long long)e << 52));
+            else z = scalbn(z, e);
+          }
+          double *zp = p.Z + row * p.ldz + col;
+          if (p.alpha == -1.0) z = -z;
+          else if (p.alpha != 1.0) z *= p.alpha;
+          if (p.beta == 1.0) z += *zp;
+          else if (p.beta != 0.0) z = fma(p.beta, *zp, z);
+          *zp = z;
+        }
       }
     }
   }
@@ -453,6 +498,17 @@ __global__ void oz_gram_finalize_kernel(int k1, int k2, int nsplit, int MR, int 
   const int ea = max(EA[si], -1100), eb = max(EB[sj], -1100);
   C[(size_t)i * ldc + j] = (ea == kENonFinite || eb == kENonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
                                                                      : scalbn(s, ea + eb - 16);
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
 }
 
 void set_smem_attrs() {
@@ -579,7 +635,9 @@ void oz_gram(int64_t n, const double *X, int ldx, int k1, const double *Y, int l
   p.part = part; p.MR = g.MR; p.NC = g.NC;
   p.err = err;
   p.run_if = run_if;
-  oz_mma_kernel<<<dim3(g.tiles, g.nsplit), 192, kMmaSmem, st>>>(p);
+  p.tiles = g.tiles;
+  p.units = g.tiles * g.nsplit;
+  oz_mma_kernel<<<std::min(p.units, num_sms()), 192, kMmaSmem, st>>>(p);
   const int64_t tot = (int64_t)k1 * k2;
   oz_gram_finalize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k1, k2, g.nsplit, g.MR, g.NC, part, EA, EB,
                                                                         sym ? 1 : 0, C, ldc, run_if);
@@ -624,7 +682,9 @@ void oz_gemm(int64_t n, const double *X, int ldx, int k1, const double *S, int l
   p.Z = Z; p.ldz = ldz; p.rows = n; p.cols = k2;
   p.alpha = alpha; p.beta = beta;
   p.err = err;
-  oz_mma_kernel<<<dim3(p.m_tiles * p.n_tiles, 1), 192, kMmaSmem, st>>>(p);
+  p.tiles = p.m_tiles * p.n_tiles;
+  p.units = p.tiles;
+  oz_mma_kernel<<<std::min(p.units, num_sms()), 192, kMmaSmem, st>>>(p);
 }
 
 }  // namespace slrf

@@ -481,7 +481,8 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   const cudaStream_t st = ctx->st;
   const int64_t n = ctx->n;
   const int L = ctx->L;
-  ctx->launches += 9;  // 3 real SpMMs, 3 Cholesky, Jacobi, 2 residual kernels; products count themselves
+  ctx->launches += 9;  // 3 SpMMs (FP32 B U, gated FP64 B U, A U1 + B U1), 3 Cholesky, Jacobi, 2 residual
+                      // kernels; the products count themselves
   // First passes in FP32 (mixed-precision CGS2 and Cholesky-QR): their Gram matrices only
   // have to bring U close to the target; the FP64 second passes remove the FP32 error.
   if (nconv > 0) {
@@ -493,10 +494,11 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   double *U1 = ctx->U2, *AU1 = ctx->AG;
   // pass 1: U1 = U R1^{-1}, R1 from the FP32 Gram; if that Gram is not numerically
   // positive definite (kappa(U) beyond ~1e3), iflags[11] triggers the FP64 Gram instead
-  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st);
+  spmm_b32(n, ctx->rowptr, ctx->col, ctx->valB, U, L, k, ctx->BU, L, st);  // FP32 B U: feeds the FP32 Gram
   cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
   tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, true);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st, nullptr, true);
+  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U, L, k, nullptr, ctx->BU, L, st, ctx->iflags + 11);
   tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, false, ctx->iflags + 11);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st, ctx->iflags + 11);
   tsgemm(ctx, n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true);
@@ -513,7 +515,16 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   tsgemm(ctx, k, ctx->Rinv, k, k, ctx->Sm, k, k, ctx->Wm, k, 1.0, 0.0, false);  // Z = R2^{-1} S
   tsgemm(ctx, n, U1, L, k, ctx->Wm, k, k, ctx->Vt, L, 1.0, 0.0, false);         // V = U1 Z
   if (want_basis) tsgemm(ctx, n, U1, L, k, ctx->Rinv, k, k, U, L, 1.0, 0.0, true);
-  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
+  if (ctx->ozwork && !want_basis) {
+    // inside the solve: A V = (A U1) Z and B V = (B U1) Z, two tensor-core products instead
+    // of an FP64 SpMM (they differ from A and B times the stored V by u |A| |V|, far below
+    // the lock tolerance); slrf_rayleigh_ritz reports the residuals of the V it returns
+    tsgemm(ctx, n, AU1, L, k, ctx->Wm, k, k, ctx->AVt, L, 1.0, 0.0, false);
+    tsgemm(ctx, n, ctx->BU, L, k, ctx->Wm, k, k, ctx->BVt, L, 1.0, 0.0, false);
+  } else {
+    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
+    ctx->launches += 1;
+  }
   ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
   CKL();
   return SLRF_OK;
