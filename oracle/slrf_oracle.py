@@ -27,7 +27,10 @@ Readings where the paper is silent (each listed in the design notes):
   * locking test: ||A v - theta B v|| / ||A v|| <= tol_eig and 0 < theta <= gamma.
   * orthogonalisation: CGS2 in the B-inner product; B-orthonormalisation: Cholesky-QR2;
     Rayleigh-Ritz on the standard problem U^T A U (U B-orthonormal).
-  * stopping: no active Ritz value <= gamma left after locking, two outer steps in a row.
+  * stopping: no active Ritz value <= gamma left after locking, two outer steps in a row,
+    each with the lowest active Ritz pair resolved (relative residual <= GUARD_RES = 1e-2):
+    the paper stops once the NEV wanted pairs converged; without NEV, an unresolved
+    subspace (short inner solves on a large mesh) can show no Ritz value <= gamma yet.
   * start block: standard Gaussian (PCG64); first-step initial guess y0 = 0.
   * eigenvector sign: the entry of largest magnitude is made positive.
 """
@@ -42,6 +45,7 @@ import scipy.sparse as sp
 # status codes mirrored by the library's documented semantics (not shared code)
 OK = 0
 E_CHOL = -6
+GUARD_RES = 1e-2  # lowest active Ritz pair must be this well resolved before the stop test counts
 E_NOCONV = -7
 
 
@@ -292,7 +296,12 @@ def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, o
             Res = np.concatenate([Res, res[conv]])
             V = V[:, ~conv]
             theta = th[~conv]
-            pending = np.any(theta <= gamma)
+            # the stop claim ("no eigenvalue <= gamma left") holds only once the subspace
+            # resolves the spectrum next to gamma: the lowest active Ritz pair must have a
+            # relative residual <= GUARD_RES (reading of the stopping rule, see module doc)
+            res_act = res[~conv]
+            unresolved = theta.size > 0 and not res_act[np.argmin(theta)] <= GUARD_RES
+            pending = bool(np.any(theta <= gamma)) or unresolved
         else:
             # Alg. 1: nothing is locked; the wanted Ritz pairs are the result once all converge
             want = (th > 0) & (th <= gamma)

@@ -709,9 +709,11 @@ __global__ void lock_decide_kernel(int k, const double *theta, const double *res
   if (threadIdx.x != 0) return;
   int n_conv = info[0];
   int newly = 0, nact = 0, pending = 0;
+  double low_th = INFINITY, low_res = 0.0;  // lowest active Ritz pair
   for (int c = 0; c < k; ++c) {
     const double th = theta[c];
     const bool conv = (res[c] <= tol) && (th > 0.0) && (th <= gamma);
+    if (!(lock && conv) && th < low_th) { low_th = th; low_res = res[c]; }
     if (lock && conv) {
       const int slot = n_conv + newly;
       dst_x[c] = slot < cap ? slot : -1;
@@ -730,6 +732,9 @@ __global__ void lock_decide_kernel(int k, const double *theta, const double *res
       }
     }
   }
+  // with locking, the stop test counts only once the subspace resolves the spectrum next
+  // to gamma: the lowest active Ritz pair has a relative residual <= 1e-2
+  if (lock && nact > 0 && !(low_res <= 1e-2)) pending = 1;
   info[0] = n_conv + newly;
   info[1] = nact;
   info[2] = pending;

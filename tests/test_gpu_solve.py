@@ -226,3 +226,20 @@ def test_solve_with_refinement_steps(slrf_mod):
     assert rc == 0 and nf == cnt
     assert np.all(np.abs(ev - lam[:cnt]) <= np.maximum(1e-8 * lam[:cnt], 1e-9 * lam[0]))
     assert rs.max() <= 1e-8
+
+
+def test_stop_rule_needs_a_resolved_subspace(slrf_mod):
+    """The oracle pin of the stopping rule on the GPU: with It_max = 2 on a 31 x 30 Q1 mesh
+    the block stays unresolved and the solve must not report success (without the resolution
+    guard it returned status OK with 0 of 10 pairs); with It_max = 5 it finds all 10, in the
+    oracle's 33 outer steps (+-1 for rounding)."""
+    p = si.q1_scalar((31, 30), dirichlet_face=(0, 0))
+    lam = sla.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    L = int(np.ceil(1.5 * cnt))
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 3, it_max=2, outer_max=30)
+    assert rc == slrf_mod.SLRF_ENOCONV
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 3, it_max=5, outer_max=60)
+    assert rc == 0 and nf == cnt
+    assert np.max(np.abs(ev - lam[:cnt]) / lam[:cnt]) <= 1e-10
+    assert abs(st["outer_iters"] - 33) <= 1

@@ -234,6 +234,26 @@ def test_solve_elasticity_against_dense_eigh():
     assert r.resid.max() <= 1e-8
 
 
+def test_stop_rule_needs_a_resolved_subspace():
+    """Inner solves far too short for the mesh (It_max = 2 on a 31 x 30 Q1 mesh) leave the
+    filtered block unresolved: no Ritz value <= gamma appears in the first outer steps.
+    Without the resolution guard the stopping rule reported success there with 0 of the 10
+    eigenpairs; with it the run does not claim success, and status OK always comes with the
+    exact count of the dense eigensolver.  A run that resolves (It_max = 5) is not delayed."""
+    p = si.q1_scalar((31, 30), dirichlet_face=(0, 0))
+    A, B = p.A(), p.B()
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    L = int(np.ceil(1.5 * cnt))
+    V1 = si.start_block(p.n, L, 3)
+    r = orc.enhanced_slrf(A, B, gamma, V1, it_max=2, outer_max=30)
+    assert r.status != orc.OK
+    r = orc.enhanced_slrf(A, B, gamma, V1, it_max=5, outer_max=60)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-10
+    assert r.outer_iters == 33
+
+
 def test_basic_method_agrees():
     """Alg. 1 (no locking, zero initial guesses, near-exact inner solves) finds the same
     eigenvalues.  With zero initial guesses the inner error is relative to ||B v||, so the
