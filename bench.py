@@ -26,6 +26,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "eigenpairs/s and shifted column-solves/s at resid≤1e-8; SpMM HBM GB/s vs peak"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz
+# DRAM bytes (read + write) of one cocg_spmm_kernel<double> launch on the 41^3 workload at
+# 160 columns x 8 poles, from the ncu capture summarised in profiles/launches_q1_lap_41_fp64.md
+SPMM64_TRAFFIC_Q1_41 = 6032729344 + 2846729984
 
 
 # Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
@@ -291,7 +294,8 @@ def main():
     if args.precision == 0:
         achieved = flops_spmm / (spmm_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": SPMM64_TRAFFIC_Q1_41 if (args.workload == "q1_lap_41" and k0 == 160 and m == 8) else None,
                 "kernel": "cocg_spmm_kernel<double>",
                 "note": ("FP64 FMA pipe bound: 8 flops/nnz/complex column + 32 flops/row/column per launch; "
                          "peak = 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (measured 1.197 TFLOP/s at 1.98 GHz)"),
