@@ -172,6 +172,8 @@ def main():
                     help="batch64: also time the plain FP64 batched solve")
     ap.add_argument("--mixed-it-max", type=int, default=15,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
+    ap.add_argument("--it-adapt", type=int, default=0,
+                    help="1: per-problem It_max grows while the lowest active Ritz pair is unresolved")
     ap.add_argument("--directions", type=int, default=8,
                     help="sens48: random directions of the finite-difference check")
     args = ap.parse_args()
@@ -365,7 +367,7 @@ def batch_bench(args, rank, world, local):
     stream = torch.cuda.Stream()
 
     def run(precision, it_max):
-        opts = slrf.slrf_opts_default(it_max=it_max, precision=precision, autotune=1)
+        opts = slrf.slrf_opts_default(it_max=it_max, precision=precision, autotune=1, it_adapt=args.it_adapt)
         with torch.cuda.stream(stream):
             b = slrf.Batch(probs, gammas, blocks, opts, stream=stream)
             for _ in range(args.warmup):
@@ -406,7 +408,8 @@ def batch_bench(args, rank, world, local):
             "config": {"workload": (f"batch64: 64 uneven scalar Q1 pencils (2D/3D, lognormal(0,0.3) coefficients, "
                                     f"sum n = {ntot}, {sum(counts)} eigenpairs, blocks 1.5x count, m=8), "
                                     f"one persistent COCG launch per phase"),
-                       "precision": "mixed (complex-FP32 COCG, FP64 outer)", "autotune": 1},
+                       "precision": "mixed (complex-FP32 COCG, FP64 outer)", "autotune": 1,
+                       "it_adapt": args.it_adapt},
             "batched_mixed": main, "batched_fp64": fp64, "gpu_launches": main["kernel_launches"], "clocks": clk}
     if rank == 0:
         print(json.dumps(line))

@@ -80,6 +80,10 @@ typedef struct {
   int autotune;           /* 1 = time candidate COCG rows-per-block at setup, keep the fastest */
   int dense;              /* products of the outer update: 1 = split-bf16 tensor-core products
                              with FP64 error (Ozaki splitting), 0 = FP64 FMA; default 1     */
+  int it_adapt;           /* 1 = per problem, It_max doubles (up to 8 it_max) after three
+                             consecutive outer steps whose lowest active Ritz pair is still
+                             unresolved (relative residual > 1e-2); 0 = fixed It_max (the
+                             paper's It_max-linear); default 0                               */
 } slrf_opts;
 
 /* Statistics of the last slrf_solve (host struct filled by the library). */
@@ -100,8 +104,8 @@ typedef struct {
 /* Fill *opts with the paper's defaults: m = 8, alpha = 1, beta = 0.01 (Sec. 3.2),
  * band = 1.3, it_max = 40, refine_max = 1, outer_max = 100, tol_inner = 1e-10 (Sec. 3.2),
  * tol_eig = 1e-8 (Sec. 3.2), precision = 0, warm_start = 1, lock = 1 (Sec. 4), use_graph = 1,
- * nev = 0, seed = 1, poles = weights = NULL, autotune = 0, dense = 1.  Returns SLRF_EINVAL
- * if opts is NULL. */
+ * nev = 0, seed = 1, poles = weights = NULL, autotune = 0, dense = 1, it_adapt = 0.  Returns
+ * SLRF_EINVAL if opts is NULL. */
 int slrf_opts_default(slrf_opts *opts);
 
 /* Create a solver context for the pencil (A, B), the interval (0, gamma] and search-block

@@ -337,6 +337,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         s.beta = cdiv(rho_new, s.rho);
         s.rho = rho_new;
       }
+      if (a.it_cap > 0 && s.iters >= a.it_cap) s.active = 0;
       if (!s.active) s.beta = make_double2(0.0, 0.0);
       a.ws[w] = s;
     }

@@ -64,6 +64,7 @@ struct CocgArgs {
   const double *valA64, *valB64;
   const double2 *sig64;
   double *r00;
+  int it_cap;  // > 0: a column stops after this many updates (per-problem It_max in a batch)
 };
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.

@@ -705,7 +705,7 @@ void ritz_residuals(int64_t n, int k, const double *V, const double *AV, const d
 // ------------------------------------------------------------------------------ locking
 __global__ void lock_decide_kernel(int k, const double *theta, const double *res, double gamma, double tol,
                                    int lock, int cap, int *info, int *dst_x, int *dst_v, double *Theta,
-                                   double *Res, double *theta_act) {
+                                   double *Res, double *theta_act, int *unresolved) {
   if (threadIdx.x != 0) return;
   int n_conv = info[0];
   int newly = 0, nact = 0, pending = 0;
@@ -734,7 +734,9 @@ __global__ void lock_decide_kernel(int k, const double *theta, const double *res
   }
   // with locking, the stop test counts only once the subspace resolves the spectrum next
   // to gamma: the lowest active Ritz pair has a relative residual <= 1e-2
-  if (lock && nact > 0 && !(low_res <= 1e-2)) pending = 1;
+  const bool unres = lock && nact > 0 && !(low_res <= 1e-2);
+  if (unres) pending = 1;
+  if (unresolved != nullptr) *unresolved = unres ? 1 : 0;
   info[0] = n_conv + newly;
   info[1] = nact;
   info[2] = pending;
@@ -742,9 +744,10 @@ __global__ void lock_decide_kernel(int k, const double *theta, const double *res
 }
 
 void lock_decide(int k, const double *theta, const double *res, double gamma, double tol, int lock, int cap,
-                 int *info, int *dst_x, int *dst_v, double *Theta, double *Res, double *theta_act, cudaStream_t st) {
+                 int *info, int *dst_x, int *dst_v, double *Theta, double *Res, double *theta_act, cudaStream_t st,
+                 int *unresolved) {
   lock_decide_kernel<<<1, 32, 0, st>>>(k, theta, res, gamma, tol, lock, cap, info, dst_x, dst_v, Theta, Res,
-                                       theta_act);
+                                       theta_act, unresolved);
 }
 
 __global__ void lock_gather_kernel(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld,

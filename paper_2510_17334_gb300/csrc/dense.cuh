@@ -64,7 +64,7 @@ size_t ritz_work_doubles(int64_t n, int k);
 // active theta to theta_act, and updates info[0..3] = {n_conv, n_act, pending, newly}.
 void lock_decide(int k, const double *theta, const double *res, double gamma, double tol, int lock,
                  int cap, int *info, int *dst_x, int *dst_v, double *Theta, double *Res, double *theta_act,
-                 cudaStream_t st);
+                 cudaStream_t st, int *unresolved = nullptr);
 // Move columns: V/AV/BV (times sgn) to X/BX (dst_x) or to Vn/AVn/BVn (dst_v).
 void lock_gather(int64_t n, int k, const double *V, const double *AV, const double *BV, int ld,
                  const double *sgn, const int *dst_x, const int *dst_v, double *X, double *BX, int ldx,

@@ -93,7 +93,9 @@ struct slrf_ctx {
   cudaEvent_t ev[4] = {};
   // graph cache of the inner loop
   cudaGraphExec_t gexec = nullptr;
-  int g_k = -1, g_warm = -1;
+  int g_k = -1, g_warm = -1, g_itm = -1;
+  int it_cur = 0;  // It_max of the next filter apply (opts.it_adapt: grows per problem)
+  int unres_streak = 0;  // consecutive outer steps with the lowest active Ritz pair unresolved
   std::vector<void *> allocs;
 };
 
@@ -274,7 +276,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   int nref = 1;
   CocgArgs<R> a = build_cocg_args<R>(ctx, X, ldx, k, U, ldu, nref);
   const int W = a.W;
-  const int itm = ctx->o.it_max;
+  const int itm = ctx->it_cur > 0 ? ctx->it_cur : ctx->o.it_max;
   const int T = W / (32 * cocg_vec<R>());  // column tiles
   // Two-group schedule (graph and direct paths, FP32 path): the tiles are split into two
   // groups that run one launch apart, so that each launch carries the SpMM of one group and
@@ -342,7 +344,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
     }
   } else if (capture_ok && ctx->o.use_graph) {
     const int warm = theta != nullptr;
-    if (!(ctx->gexec && ctx->g_k == k && ctx->g_warm == warm)) {
+    if (!(ctx->gexec && ctx->g_k == k && ctx->g_warm == warm && ctx->g_itm == itm)) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -353,6 +355,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
       if (e != cudaSuccess) { ctx->status = SLRF_ECUDA; return SLRF_ECUDA; }
       ctx->g_k = k;
       ctx->g_warm = warm;
+      ctx->g_itm = itm;
     }
     CK(cudaGraphLaunch(ctx->gexec, ctx->st));
   } else {
@@ -438,6 +441,17 @@ static int autotune_rows(slrf_ctx *ctx) {
   ctx->rpb_tuned = best_r;
   CKL();
   return SLRF_OK;
+}
+
+// opts.it_adapt: after three consecutive outer steps whose lowest active Ritz pair is still
+// unresolved (relative residual > 1e-2), the problem's It_max doubles, up to 8 opts.it_max.
+static void adapt_it(slrf_ctx *c, bool unresolved) {
+  if (!c->o.it_adapt) return;
+  if (!unresolved) { c->unres_streak = 0; return; }
+  if (++c->unres_streak >= 3) {
+    c->it_cur = std::min(2 * c->it_cur, 8 * c->o.it_max);
+    c->unres_streak = 0;
+  }
 }
 
 // ----------------------------------------------------------------------------- products
@@ -542,7 +556,7 @@ struct slrf_batch {
   void *dargs = nullptr, *hargs = nullptr;
   int *dprefix = nullptr, *hprefix = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  int g_P = -1, g_total = -1;
+  int g_P = -1, g_total = -1, g_itm = -1;
 };
 
 static void batch_free(slrf_batch *b) {
@@ -586,7 +600,7 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
   slrf_ctx *ctx = nullptr;  // for CK
   const int vec = cocg_vec<R>();
   CocgArgs<R> *ha = reinterpret_cast<CocgArgs<R> *>(b->hargs);
-  int nref = 1, total = 0;
+  int nref = 1, total = 0, itm = 0;
   const int P = (int)act.size();
   b->hprefix[0] = 0;
   for (int i = 0; i < P; ++i) {
@@ -596,6 +610,8 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
     int rc = filter_prep(c, c->V, c->L, k, th, warm[act[i]] ? c->AV : nullptr, warm[act[i]] ? c->BV : nullptr);
     if (rc != SLRF_OK) return rc;
     ha[i] = build_cocg_args<R>(c, c->V, c->L, k, c->U, c->L, nref);
+    ha[i].it_cap = c->o.it_adapt ? c->it_cur : 0;  // per-problem It_max inside the shared loop
+    itm = std::max(itm, c->it_cur > 0 ? c->it_cur : c->o.it_max);
     cocg_prepare(ha[i].W, k, c->m, c->mp, c->sig, c->wt, th, c->cfac, c->coefV, c->ws, c->st);
     if (sizeof(R) == 4) col_scale(c->n, k, c->G, c->L, c->gmax, c->gscale, c->st);
     launches += 1 + (sizeof(R) == 4 ? 2 : 0);
@@ -604,12 +620,11 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
     CK(cudaEventRecord(b->ev_p[act[i]], c->st));
     CK(cudaStreamWaitEvent(b->st, b->ev_p[act[i]], 0));
   }
-  const int itm = b->c[act[0]]->o.it_max;
   CK(cudaMemcpyAsync(b->dargs, b->hargs, P * sizeof(CocgArgs<R>), cudaMemcpyHostToDevice, b->st));
   CK(cudaMemcpyAsync(b->dprefix, b->hprefix, (P + 1) * sizeof(int), cudaMemcpyHostToDevice, b->st));
   launches += 1 + (int64_t)nref * (2 * itm - 1) + (nref - 1) * (sizeof(R) == 4 ? 2 : 1);
   if (b->c[act[0]]->o.use_graph) {
-    if (!(b->gexec && b->g_P == P && b->g_total == total)) {
+    if (!(b->gexec && b->g_P == P && b->g_total == total && b->g_itm == itm)) {
       if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
@@ -620,6 +635,7 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
       if (e != cudaSuccess) return SLRF_ECUDA;
       b->g_P = P;
       b->g_total = total;
+      b->g_itm = itm;
     }
     CK(cudaGraphLaunch(b->gexec, b->st));
   } else {
@@ -749,7 +765,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   slrf_opts o;
   if (opts) o = *opts;
   else slrf_opts_default(&o);
-  if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1 || o.dense < 0 || o.dense > 1)
+  if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1 || o.dense < 0 || o.dense > 1 ||
+      o.it_adapt < 0 || o.it_adapt > 1)
     return SLRF_EINVAL;
   if (block_L > 510) return SLRF_EINVAL;  // the projected eigensolver holds two rows of <= 512 in shared memory
   if (!(o.tol_inner >= 0) || !(o.tol_eig > 0)) return SLRF_EINVAL;
@@ -1053,6 +1070,12 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
   }
   int k = L, nconv = 0, quiet = 0, status = SLRF_ENOCONV, outer = 0;
   ctx->launches = V0 ? 2 : 1;
+  ctx->it_cur = ctx->o.it_max;
+  ctx->unres_streak = 0;
+  struct ItReset {
+    slrf_ctx *c;
+    ~ItReset() { c->it_cur = 0; }  // filter_apply outside a solve uses opts.it_max
+  } it_reset{ctx};
   bool have_ritz = false;
   float ms_f = 0, ms_d = 0;
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -1070,7 +1093,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
     if (rc != SLRF_OK) return rc;
     // lock decision, compaction (the locking step of Alg. 2)
     lock_decide(k, ctx->theta, ctx->res, ctx->gamma, ctx->o.tol_eig, ctx->o.lock, L, ctx->iflags, ctx->dst_x,
-                ctx->dst_v, ctx->Theta, ctx->Res, ctx->theta_act, st);
+                ctx->dst_v, ctx->Theta, ctx->Res, ctx->theta_act, st, ctx->iflags + 14);
     lock_gather(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->sgn, ctx->dst_x, ctx->dst_v, ctx->X, ctx->BX, L, ctx->V,
                 ctx->AV, ctx->BV, L, st);
     CKL();
@@ -1091,6 +1114,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
     k = hf[1];
     const int pending = hf[2];
     have_ritz = true;
+    adapt_it(ctx, hf[14] != 0);
     if (k < 1) { status = SLRF_OK; break; }
     quiet = pending ? 0 : quiet + 1;
     if (quiet >= 2 && (ctx->o.nev <= 0 || nconv >= ctx->o.nev)) { status = SLRF_OK; break; }
@@ -1254,8 +1278,14 @@ int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, 
     if (V0 && V0[p]) copy_block(c->n, c->L, V0[p], c->L, c->V, c->L, c->st);
     else gaussian_block(c->n, c->L, c->o.seed + p, c->V, c->L, c->st);
     CK(cudaMemsetAsync(c->iflags, 0, 16 * sizeof(int), c->st));
+    c->it_cur = c->o.it_max;
+    c->unres_streak = 0;
     launches += 1;
   }
+  struct ItReset {
+    slrf_batch *b;
+    ~ItReset() { for (auto *c : b->c) c->it_cur = 0; }
+  } it_reset{b};
   const int outer_max = b->c[0]->o.outer_max;
   int outer = 0;
   for (outer = 1; outer <= outer_max; ++outer) {
@@ -1274,7 +1304,7 @@ int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, 
       int r2 = rr_impl(c, c->U, k, c->X, c->BX, c->o.lock ? nconv[p] : 0, c->L);
       if (r2 != SLRF_OK) return r2;
       lock_decide(k, c->theta, c->res, c->gamma, c->o.tol_eig, c->o.lock, c->L, c->iflags, c->dst_x, c->dst_v,
-                  c->Theta, c->Res, c->theta_act, c->st);
+                  c->Theta, c->Res, c->theta_act, c->st, c->iflags + 14);
       lock_gather(c->n, k, c->Vt, c->AVt, c->BVt, c->L, c->sgn, c->dst_x, c->dst_v, c->X, c->BX, c->L, c->V, c->AV,
                   c->BV, c->L, c->st);
       CK(cudaMemcpyAsync(c->h_iflags, c->iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1291,6 +1321,7 @@ int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, 
       kk[p] = hf[1];
       warm[p] = c->o.warm_start ? 1 : 0;
       if (kk[p] < 1) { st_p[p] = SLRF_OK; done[p] = 1; continue; }
+      adapt_it(c, hf[14] != 0);
       quiet[p] = hf[2] ? 0 : quiet[p] + 1;
       if (quiet[p] >= 2 && (c->o.nev <= 0 || nconv[p] >= c->o.nev)) { st_p[p] = SLRF_OK; done[p] = 1; }
     }

@@ -52,7 +52,7 @@ class Opts(ct.Structure):
                 ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
                 ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
                 ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int),
-                ("dense", ct.c_int)]
+                ("dense", ct.c_int), ("it_adapt", ct.c_int)]
 
 
 class Stats(ct.Structure):

@@ -73,3 +73,28 @@ def test_autotuned_setup_solves_correctly(slrf_mod):
     assert rc == 0 and nf == cnt
     assert np.all(np.abs(ev - lam[:cnt]) <= np.maximum(1e-10 * lam[:cnt], 1e-9 * lam[0]))
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_adaptive_it_max(slrf_mod, precision):
+    """A batch whose shared start It_max (3) is too short for one of its problems (the 31 x 30
+    mesh): with opts.it_adapt each problem's It_max grows on its own and every problem
+    returns its exact count; the fast problems keep their short solves."""
+    probs = _problems()[:3]
+    p = si.q1_scalar((31, 30), dirichlet_face=(0, 0))
+    lam = sla.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    probs.append((p, lam, gamma, cnt, int(np.ceil(1.5 * cnt))))
+    opts = slrf_mod.slrf_opts_default(it_max=3, it_adapt=1, precision=precision, outer_max=150)
+    V0 = [si.start_block(q.n, L, 20 + i) for i, (q, _, _, _, L) in enumerate(probs)]
+    batch = slrf_mod.Batch([(q.rowptr, q.col, q.valA, q.valB) for q, *_ in probs], [g for _, _, g, _, _ in probs],
+                           [L for *_, L in probs], opts)
+    rc, res, st = batch.solve(V0)
+    assert rc == 0
+    tol = 1e-10 if precision == 0 else 1e-8
+    for (q, lam_q, g, c, L), (status, nf, ev, X, rs) in zip(probs, res):
+        ev = ev.cpu().numpy()
+        assert status == 0 and nf == c
+        assert np.all(np.abs(ev - lam_q[:c]) <= np.maximum(tol * lam_q[:c], 1e-9 * lam_q[0]))
+        assert rs.max().item() <= 1e-8
+    batch.close()

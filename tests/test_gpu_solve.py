@@ -243,3 +243,17 @@ def test_stop_rule_needs_a_resolved_subspace(slrf_mod):
     assert rc == 0 and nf == cnt
     assert np.max(np.abs(ev - lam[:cnt]) / lam[:cnt]) <= 1e-10
     assert abs(st["outer_iters"] - 33) <= 1
+
+
+def test_adaptive_it_max_resolves_short_inner_solves(slrf_mod):
+    """opts.it_adapt: the same 31 x 30 mesh from It_max = 2, which alone ends unresolved;
+    the problem's It_max doubles while its lowest active Ritz pair stays unresolved, and the
+    solve finds all 10 pairs."""
+    p = si.q1_scalar((31, 30), dirichlet_face=(0, 0))
+    lam = sla.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    L = int(np.ceil(1.5 * cnt))
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, p, gamma, L, 3, it_max=2, it_adapt=1, outer_max=100)
+    assert rc == 0 and nf == cnt
+    assert np.max(np.abs(ev - lam[:cnt]) / lam[:cnt]) <= 1e-10
+    assert rs.max() <= 1e-8
