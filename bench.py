@@ -172,6 +172,8 @@ def main():
                     help="batch64: also time the plain FP64 batched solve")
     ap.add_argument("--mixed-it-max", type=int, default=15,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
+    ap.add_argument("--dense", type=int, default=1,
+                    help="1: FP64-accurate split-bf16 tensor-core products in the outer update; 0: FP64 FMA")
     ap.add_argument("--it-adapt", type=int, default=0,
                     help="1: per-problem It_max grows while the lowest active Ritz pair is unresolved")
     ap.add_argument("--directions", type=int, default=8,
@@ -205,7 +207,7 @@ def main():
 
     wl, desc = workload(args.workload, args.it_max)
     p = wl.pencil
-    opts = slrf.slrf_opts_default(m=wl.m, it_max=wl.it_max, precision=args.precision)
+    opts = slrf.slrf_opts_default(m=wl.m, it_max=wl.it_max, precision=args.precision, dense=args.dense)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, opts, stream=stream)
@@ -367,7 +369,8 @@ def batch_bench(args, rank, world, local):
     stream = torch.cuda.Stream()
 
     def run(precision, it_max):
-        opts = slrf.slrf_opts_default(it_max=it_max, precision=precision, autotune=1, it_adapt=args.it_adapt)
+        opts = slrf.slrf_opts_default(it_max=it_max, precision=precision, autotune=1, it_adapt=args.it_adapt,
+                                      dense=args.dense)
         with torch.cuda.stream(stream):
             b = slrf.Batch(probs, gammas, blocks, opts, stream=stream)
             for _ in range(args.warmup):

@@ -457,10 +457,17 @@ static void adapt_it(slrf_ctx *c, bool unresolved) {
 // ----------------------------------------------------------------------------- products
 // Tall-skinny products of the outer update: split-bf16 tensor-core products with the error
 // of an FP64 product (opts.dense = 1) or FP64 FMA on the CUDA cores.  FP32 first passes
-// stay on the CUDA cores.  Each adds the kernels it launches to ctx->launches.
+// stay on the CUDA cores, and so do tall products (n > 4096) below kOzMinWork = n k1 k2
+// multiply-adds, where the FP64 product (~2 n k1 k2 / 1e12 s) beats the fixed ~80 us of the
+// split path's launches (the small k x k products keep the split path: the FP64 kernels
+// would run on a handful of blocks).  Each adds the kernels it launches to ctx->launches.
+constexpr double kOzMinWork = 5e7;
+static bool use_split(const slrf_ctx *ctx, int64_t n, int k1, int k2) {
+  return ctx->ozwork != nullptr && (n <= 4096 || (double)n * k1 * k2 >= kOzMinWork);
+}
 static void tsgram(slrf_ctx *ctx, int64_t n, const double *X, int ldx, int k1, const double *Y, int ldy, int k2,
                    double *C, int ldc, bool sym, bool fp32 = false, const int *run_if = nullptr) {
-  if (ctx->ozwork && !fp32) {
+  if (!fp32 && use_split(ctx, n, k1, k2)) {
     const bool same = X == Y && ldx == ldy && k1 == k2;
     oz_gram(n, X, ldx, k1, Y, ldy, k2, C, ldc, sym, ctx->ozwork, ctx->ozwork_bytes, ctx->iflags + 13, ctx->st,
             run_if);
@@ -472,7 +479,7 @@ static void tsgram(slrf_ctx *ctx, int64_t n, const double *X, int ldx, int k1, c
 }
 static void tsgemm(slrf_ctx *ctx, int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2,
                    double *Z, int ldz, double alpha, double beta, bool upper) {
-  if (ctx->ozwork) {
+  if (use_split(ctx, n, k1, k2)) {
     oz_gemm(n, X, ldx, k1, S, lds, k2, Z, ldz, alpha, beta, ctx->ozwork, ctx->ozwork_bytes, ctx->iflags + 13,
             ctx->st);
     ctx->launches += 4;
@@ -529,7 +536,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   tsgemm(ctx, k, ctx->Rinv, k, k, ctx->Sm, k, k, ctx->Wm, k, 1.0, 0.0, false);  // Z = R2^{-1} S
   tsgemm(ctx, n, U1, L, k, ctx->Wm, k, k, ctx->Vt, L, 1.0, 0.0, false);         // V = U1 Z
   if (want_basis) tsgemm(ctx, n, U1, L, k, ctx->Rinv, k, k, U, L, 1.0, 0.0, true);
-  if (ctx->ozwork && !want_basis) {
+  if (!want_basis && use_split(ctx, n, k, k)) {
     // inside the solve: A V = (A U1) Z and B V = (B U1) Z, two tensor-core products instead
     // of an FP64 SpMM (they differ from A and B times the stored V by u |A| |V|, far below
     // the lock tolerance); slrf_rayleigh_ritz reports the residuals of the V it returns
