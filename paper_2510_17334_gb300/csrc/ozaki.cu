@@ -451,6 +451,9 @@ __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
         for (int qq = 0; qq < 32; ++qq) dst[qq] = fma((double)I[qq], 0x1p-32, (double)f5[qq]);
       } else if (row < p.rows) {
         const int ea = max(p.EA[row], -1100);
+        // uniform flags, decided once (FP64 compares run on the FP64 pipe)
+        const int amode = p.alpha == 1.0 ? 0 : (p.alpha == -1.0 ? 1 : 2);
+        const int bmode = p.beta == 0.0 ? 0 : (p.beta == 1.0 ? 1 : 2);
 #pragma unroll
         for (int qq = 0; qq < 32; ++qq) {
           const int col = kTN * u + qq;
@@ -458,18 +461,20 @@ __global__ void __launch_bounds__(192, 1) oz_mma_kernel(const OzMma p) {
           const int eb = max(p.EB[col], -1100);
           double z = fma((double)f5[qq], 4294967296.0, (double)I[qq]);  // in units of 2^-32
           const int e = ea + eb - 48;  // value = z 2^(EA + EB - 16 - 32)
+          long long zb = __double_as_longlong(z);
           if (ea == kENonFinite || eb == kENonFinite) {
-            z = __longlong_as_double(0x7ff8000000000000ll);
-          } else if (z != 0.0) {
-            const int ez = (int)((__double_as_longlong(z) >> 52) & 0x7FF);  // biased exponent of z (>= 1023)
-            if (ez + e >= 1 && ez + e <= 2046) z = __longlong_as_double(__double_as_longlong(z) + ((long long)e << 52));
-            else z = scalbn(z, e);
+            zb = 0x7ff8000000000000ll;
+          } else if ((zb & 0x7FFFFFFFFFFFFFFFll) != 0) {
+            const int ez = (int)((zb >> 52) & 0x7FF);  // biased exponent of z (>= 1023)
+            if (ez + e >= 1 && ez + e <= 2046) zb += (long long)e << 52;
+            else zb = __double_as_longlong(scalbn(z, e));
           }
+          if (amode == 1) zb ^= (long long)0x8000000000000000ull;  // alpha = -1: flip the sign bit
+          z = __longlong_as_double(zb);
+          if (amode == 2) z *= p.alpha;
           double *zp = p.Z + row * p.ldz + col;
-          if (p.alpha == -1.0) z = -z;
-          else if (p.alpha != 1.0) z *= p.alpha;
-          if (p.beta == 1.0) z += *zp;
-          else if (p.beta != 0.0) z = fma(p.beta, *zp, z);
+          if (bmode == 1) z += *zp;
+          else if (bmode == 2) z = fma(p.beta, *zp, z);
           *zp = z;
         }
       }
