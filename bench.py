@@ -34,7 +34,7 @@ SPMM64_TRAFFIC_Q1_41 = 6032729344 + 2846729984
 # Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
 # over all (pole, column) systems and outer iterations), used to scale the timed oracle
 # sample of the reference arm to a whole solve.
-SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 17, "column_iterations": 166560},
+SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 18, "column_iterations": 145920},
                 "bar1d_2000": {"n_found": 20, "outer": 8, "column_iterations": 358400},
                 "elast_32": {"n_found": 60, "outer": 20, "column_iterations": 448640}}
 
@@ -44,7 +44,7 @@ def workload(name: str, it_max: int | None):
 
     if name == "q1_lap_41":
         wl = si.q1_lap(41)
-        wl.it_max = it_max or 10
+        wl.it_max = it_max or 8
         desc = ("3D Q1 Laplacian + consistent mass, 41^3 nodes (n=68,921, 27 nnz/row), Neumann + 1e-3 B, "
                 "gamma=259.0666 (105 eigenpairs), block 160, m=8")
     elif name.startswith("q1_lap_"):
@@ -170,7 +170,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch64: also time the plain FP64 batched solve")
-    ap.add_argument("--mixed-it-max", type=int, default=15,
+    ap.add_argument("--mixed-it-max", type=int, default=8,
                     help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
     ap.add_argument("--dense", type=int, default=1,
                     help="1: FP64-accurate split-bf16 tensor-core products in the outer update; 0: FP64 FMA")
