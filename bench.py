@@ -39,6 +39,21 @@ SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 18, "column_iterations": 
                 "elast_32": {"n_found": 60, "outer": 20, "column_iterations": 448640}}
 
 
+def reduce_over_ranks(found: int, ms: float, world: int, device: str = "cuda"):
+    """Whole-job totals of N independent replicas (one per GPU): eigenpairs summed over the
+    ranks, time = the slowest rank's.  world == 1 returns the inputs."""
+    if world <= 1:
+        return found, ms
+    import torch
+    import torch.distributed as dist
+
+    f = torch.tensor([float(found)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return int(round(f.item())), float(m.item())
+
+
 def workload(name: str, it_max: int | None):
     import slrf_inputs as si
 
@@ -238,10 +253,7 @@ def main():
         barrier()
         clk = clocks_stop(cp, cf, local)
         ms = e0.elapsed_time(e1)
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
+        total_found, ms_max = reduce_over_ranks(sum(found), ms, world)
         rc, nf, ev, X, rs, st = last
         maxres = float(rs.max().item())
         # kernel-level roofline of the dominant kernel (the fused shifted SpMM + COCG phase 1)
@@ -277,15 +289,15 @@ def main():
             mev = mres[2].cpu().numpy()
             fev = ev.cpu().numpy()
             dev_ = float(np.max(np.abs(mev - fev) / fev)) if len(mev) == len(fev) else None
-            mixed = {"value": sum(mfound) * world / (mms / 1e3), "unit": "eigenpairs/s", "it_max": args.mixed_it_max,
+            mtot, mms = reduce_over_ranks(sum(mfound), mms, world)
+            mixed = {"value": mtot / (mms / 1e3), "unit": "eigenpairs/s", "it_max": args.mixed_it_max,
                      "ms_per_step": mms / args.steps, "eigenpairs_found": mres[1],
                      "max_resid": float(mres[4].max().item()),
                      "max_rel_eig_diff_vs_fp64": dev_, "outer_iters": mres[5]["outer_iters"],
                      "ms_filter_per_step": mres[5]["ms_filter"], "ms_dense_per_step": mres[5]["ms_dense"]}
             mctx.close()
 
-    total_pairs = sum(found) * world
-    value = total_pairs / (ms_max / 1e3)
+    value = total_found / (ms_max / 1e3)
     col_solves = sum(s["column_solves"] for s in stats)
     col_iters = sum(s["column_iterations"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
