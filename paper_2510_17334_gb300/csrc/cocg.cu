@@ -32,6 +32,14 @@
 #ifndef SLRF_GATHER_UNROLL
 #define SLRF_GATHER_UNROLL 8
 #endif
+// CSR entries of a row chunk from shared-memory records (1) or register shuffles (0):
+// records win in FP64 (five shuffles per entry), shuffles by a little in FP32
+#ifndef SLRF_SPMM_SREC64
+#define SLRF_SPMM_SREC64 1
+#endif
+#ifndef SLRF_SPMM_SREC32
+#define SLRF_SPMM_SREC32 0
+#endif
 namespace slrf {
 constexpr int kGatherUnroll = SLRF_GATHER_UNROLL;  // CSR entries of a row in flight per warp
 }
@@ -345,6 +353,33 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
 }
 
 // ------------------------------------------------------------------------------ spmm
+// One CSR entry of a row chunk as the SpMM reads it from shared memory: a 16-byte record
+// (FP32: column, a, b) or 24 bytes (FP64: a, b as a 16-byte pair, then the column).
+template <typename R> struct SRec;
+template <> struct alignas(16) SRec<float> { int c; float a, b, pad; };
+template <> struct alignas(16) SRec<double> { double2 ab; int c, pad0, pad1, pad2; };
+template <typename R> __device__ __forceinline__ void srec_put(SRec<R> *r, int lane, int c, R av, R bv);
+template <> __device__ __forceinline__ void srec_put<float>(SRec<float> *r, int lane, int c, float av, float bv) {
+  *reinterpret_cast<float4 *>(r + lane) = make_float4(__int_as_float(c), av, bv, 0.f);
+}
+template <> __device__ __forceinline__ void srec_put<double>(SRec<double> *r, int lane, int c, double av, double bv) {
+  r[lane].ab = make_double2(av, bv);
+  r[lane].c = c;
+}
+template <typename R> __device__ __forceinline__ void srec_get(const SRec<R> *r, int t, int &c, R &av, R &bv);
+template <> __device__ __forceinline__ void srec_get<float>(const SRec<float> *r, int t, int &c, float &av, float &bv) {
+  const float4 v = *reinterpret_cast<const float4 *>(r + t);
+  c = __float_as_int(v.x);
+  av = v.y;
+  bv = v.z;
+}
+template <> __device__ __forceinline__ void srec_get<double>(const SRec<double> *r, int t, int &c, double &av, double &bv) {
+  const double2 ab = r[t].ab;
+  c = r[t].c;
+  av = ab.x;
+  bv = ab.y;
+}
+
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
 template <typename R, bool FRESH>
 __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int rb, const int tile) {
@@ -353,6 +388,9 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
+  constexpr bool kSrec = sizeof(R) == 8 ? SLRF_SPMM_SREC64 != 0 : SLRF_SPMM_SREC32 != 0;
+  __shared__ SRec<R> srec_all[kSrec ? kWarps * 32 : 1];
+  SRec<R> *const srec = srec_all + (kSrec ? warp * 32 : 0);
   C sg[VEC], be[VEC];
   bool act[VEC];
   bool any_act = false;
@@ -376,6 +414,8 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   if (warp_act) {
     // s = (A - sigma B) r for one row (sa = A r, sb = B r), lanes over this warp's columns
+    const char *const rlane = reinterpret_cast<const char *>(a.r + w0);
+    const unsigned wbytes = (unsigned)a.W * (unsigned)sizeof(C);
     auto gather_row = [&](int64_t i, C (&sa)[VEC], C (&sb)[VEC]) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) { sa[v] = cmake<C>(0, 0); sb[v] = cmake<C>(0, 0); }
@@ -385,12 +425,27 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
         int cl = 0;
         R avl = 0, bvl = 0;
         if (lane < cnt) { cl = a.col[e0 + lane]; avl = a.valA[e0 + lane]; bvl = a.valB[e0 + lane]; }
+        if constexpr (kSrec) {
+          // the warp's chunk of (column, a, b) goes to shared memory once; every entry is
+          // then one broadcast shared load instead of three (FP64: five) register shuffles,
+          // which share the load/store pipe with the gathers
+          __syncwarp();
+          srec_put<R>(srec, lane, cl, avl, bvl);
+          __syncwarp();
+        }
 #pragma unroll kGatherUnroll
         for (int t = 0; t < cnt; ++t) {
-          const int c = __shfl_sync(0xffffffffu, cl, t);
-          const R av = __shfl_sync(0xffffffffu, avl, t);
-          const R bv = __shfl_sync(0xffffffffu, bvl, t);
-          const Vec<R> x = ldv<R>(a.r + (size_t)c * a.W + w0);
+          int c;
+          R av, bv;
+          if constexpr (kSrec) {
+            srec_get<R>(srec, t, c, av, bv);
+          } else {
+            c = __shfl_sync(0xffffffffu, cl, t);
+            av = __shfl_sync(0xffffffffu, avl, t);
+            bv = __shfl_sync(0xffffffffu, bvl, t);
+          }
+          // byte offset c * W * sizeof(C) as one 32 x 32 -> 64-bit multiply-add (c >= 0)
+          const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
             sa[v].x = fma(av, x.z[v].x, sa[v].x);
