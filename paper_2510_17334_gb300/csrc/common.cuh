@@ -69,39 +69,40 @@ __device__ __forceinline__ bool last_block_arrive(unsigned *counter, unsigned to
 }
 
 // ---------------------------------------------------------------- bounded grid barrier
-// For cooperative launches only (all blocks co-resident).  *count and *gen live in
-// global memory and start at 0.  A block that waits longer than the spin limit sets
-// *err = 1 and returns false; callers leave the kernel when it returns false.
+// For cooperative launches only (all blocks co-resident).  *count lives in global memory
+// and starts at 0; it only grows: barrier number e (1, 2, ...) is complete once it holds
+// e * nblocks, so an arrival is one fire-and-forget add after the block's stores are
+// fenced, and a waiter polls one word (no reset, no second counter on the critical path).
+// A block that waits longer than the spin limit sets *err = 1 and returns false; a block
+// that sees *err set returns false too; callers leave the kernel when it returns false.
 struct GridBarrier {
   unsigned *count;
-  unsigned *gen;
   int *err;
 };
 
-__device__ inline bool grid_sync(const GridBarrier &gb, unsigned nblocks) {
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ inline bool grid_sync(const GridBarrier &gb, unsigned nblocks, unsigned &epoch) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned *vgen = gb.gen;
-    unsigned g = *vgen;
     __threadfence();
-    unsigned arrived = atomicAdd(gb.count, 1u);
-    if (arrived == nblocks - 1u) {
-      *gb.count = 0u;
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if ((++spins & 63) == 0) {
-          if (*(volatile int *)gb.err) { ok = 0; break; }
-          if (spins > (1ll << 22)) { atomicExch(gb.err, 1); ok = 0; break; }  // a few seconds of polls
-          __nanosleep(32);
-        }
+    atomicAdd(gb.count, 1u);
+    const unsigned target = epoch * nblocks;
+    long long spins = 0;
+    while ((int)(ld_acquire_gpu(gb.count) - target) < 0) {
+      if ((++spins & 63) == 0) {
+        if (*(volatile int *)gb.err) { ok = 0; break; }
+        if (spins > (1ll << 22)) { atomicExch(gb.err, 1); ok = 0; break; }  // a few seconds of polls
+        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;

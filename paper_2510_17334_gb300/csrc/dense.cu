@@ -505,11 +505,15 @@ void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cud
 
 // ------------------------------------------------------------------------------ Jacobi
 // Two-sided cyclic Jacobi with the round-robin (circle) ordering, which makes the kk/2
-// rotations of one round disjoint.  Every block computes all rotations of the round
-// (cheap 2x2 problems), then rewrites the rows p, q of J^T A J and of V^T for the pairs
-// it owns; one grid barrier per round.  The sweep loop stops once the largest relative
-// off-diagonal met in a sweep is below 1e-8 (quadratic convergence leaves it at rounding
-// level after that sweep).
+// rotations of one round disjoint.  One block per pair: every block computes all rotations
+// of the round (cheap 2x2 problems), then rewrites the rows p, q of J^T A J and of V^T for
+// its own pair; one grid barrier per round.  The rotation inputs of a round (a_pp, a_qq,
+// a_pq of every pair) are not read from A, whose rows the owning blocks rewrite during the
+// round, but from a small table that the owners of the previous round filled (two copies,
+// alternating by round), and the block's own rows load together with them: a round costs
+// one L2 round trip, the rotation arithmetic and the barrier.  The sweep loop stops once
+// every off-diagonal met in a sweep is below 1e-8 of its diagonal scale (quadratic
+// convergence leaves them at rounding level after that sweep).
 __device__ __forceinline__ void rr_pair(int kk, int r, int b, int &p, int &q) {
   const int M = kk - 1;
   int a0, a1;
@@ -525,61 +529,98 @@ __device__ __forceinline__ int rr_partner(int kk, int r, int x) {
   return ((2 * r - x) % M + M) % M;
 }
 
-__global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double *H, int ldh, double *theta,
-                                                     double *S, int lds, JacobiWork w, int max_sweeps) {
-  const unsigned nb = gridDim.x;
-  GridBarrier gb{w.bar, w.bar + 1, w.err};
+// Rotation (c, s) that annihilates a_pq: t = tan(phi) is the smaller root of
+// t^2 + 2 tau t - 1 = 0 with tau = (a_qq - a_pp) / (2 a_pq), written as
+// t = sgn(th) ph / (|th| + sqrt(th^2 + ph^2)) with th = a_qq - a_pp, ph = 2 a_pq
+// (t = 1 when th = 0), then c = 1 / sqrt(1 + t^2), s = t c.
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double &c, double &sn) {
+  const double th = aqq - app, ph = 2.0 * apq;
+  double t;
+  if (fmax(fabs(th), fabs(ph)) < 1e150) {
+    const double num = th > 0.0 ? ph : (th < 0.0 ? -ph : fabs(ph));
+    t = num / (fabs(th) + sqrt(th * th + ph * ph));
+  } else {  // squares would overflow
+    const double tau = th / ph;
+    t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  }
+  c = rsqrt(1.0 + t * t);
+  sn = t * c;
+}
+
+constexpr int kJacobiThreads = 128;
+constexpr int kJacobiPer = 512 / kJacobiThreads;  // row entries per thread (kk <= 512)
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(int k, int kk, const double *H, int ldh,
+                                                                double *theta, double *S, int lds, JacobiWork w,
+                                                                int max_sweeps) {
+  const unsigned nb = gridDim.x;  // == kk / 2: block b owns pair b of every round
+  GridBarrier gb{w.bar, w.err};
+  unsigned epoch = 0;
   double *A = w.A, *Vt = w.Vt;
+  double *const rdiag = w.rot, *const roff = w.rot + 2 * kk;  // [2][kk] each
   // init: A = H (padded), Vt = I
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)kk * kk;
        t += (int64_t)nb * blockDim.x) {
     const int i = (int)(t / kk), j = (int)(t % kk);
-    A[t] = (i < k && j < k) ? H[(size_t)i * ldh + j] : 0.0;
+    const double h = (i < k && j < k) ? H[(size_t)i * ldh + j] : 0.0;
+    A[t] = h;
     Vt[t] = (i == j) ? 1.0 : 0.0;
+    // the round-0 table: diagonal, and a_pq of every round-0 pair (p < q) at index p
+    if (i == j) rdiag[i] = h;
+    else if (i < j && rr_partner(kk, 0, i) == j) roff[i] = h;
   }
-  if (!grid_sync(gb, nb)) return;
-  __shared__ double rp[512], rq[512];  // kk <= 512
+  if (!grid_sync(gb, nb, epoch)) return;
+  __shared__ double rp[512], rq[512];  // rows p, q of A
   __shared__ double cs[512][2];        // rotation (c, s) of every index for this round
-  __shared__ double red[128];
+  const int b0 = blockIdx.x;
+  int par = 0;  // table copy of the current round
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // largest |a_pq| / sqrt(|a_pp a_qq|) met this sweep (per thread, reduced once per sweep;
-    // identical in every block since every block computes every rotation)
-    double my_off = 0.0;
+    // has this thread met |a_pq| >= 1e-8 sqrt(|a_pp a_qq|) this sweep?  (identical in every
+    // block, since every block computes every rotation)
+    int unconv = 0;
     for (int r = 0; r < kk - 1; ++r) {
+      int p, q;
+      rr_pair(kk, r, b0, p, q);
+      // this block's rows of A and V^T, in flight while the rotation inputs load
+      double ap[kJacobiPer], aq[kJacobiPer], vp[kJacobiPer], vq[kJacobiPer];
+#pragma unroll
+      for (int u = 0; u < kJacobiPer; ++u) {
+        const int x = threadIdx.x + u * kJacobiThreads;
+        if (x < kk) {
+          ap[u] = __ldcg(&A[(size_t)p * kk + x]);
+          aq[u] = __ldcg(&A[(size_t)q * kk + x]);
+          vp[u] = __ldcg(&Vt[(size_t)p * kk + x]);
+          vq[u] = __ldcg(&Vt[(size_t)q * kk + x]);
+        }
+      }
       // every block computes every rotation of the round (kk/2 independent 2x2 problems),
       // so no barrier is needed between the rotation and the update phase
       for (int b = threadIdx.x; b < kk / 2; b += blockDim.x) {
-        int p, q;
-        rr_pair(kk, r, b, p, q);
-        const double app = __ldcg(&A[(size_t)p * kk + p]), aqq = __ldcg(&A[(size_t)q * kk + q]),
-                     apq = __ldcg(&A[(size_t)p * kk + q]);
+        int pb, qb;
+        rr_pair(kk, r, b, pb, qb);
+        const double app = __ldcg(&rdiag[par * kk + pb]), aqq = __ldcg(&rdiag[par * kk + qb]),
+                     apq = __ldcg(&roff[par * kk + pb]);
+        const double a2 = apq * apq, sc2 = fabs(app * aqq);
+        unconv |= (apq != 0.0 && a2 >= 1e-16 * sc2);
         double c = 1.0, sn = 0.0;
-        const double scale = sqrt(fabs(app * aqq));
-        const double rel = scale > 0.0 ? fabs(apq) / scale : (apq != 0.0 ? 1.0 : 0.0);
-        my_off = fmax(my_off, rel);
-        if (apq != 0.0 && fabs(apq) > 1e-15 * scale) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          sn = t * c;
-        }
-        cs[p][0] = c; cs[p][1] = sn;
-        cs[q][0] = c; cs[q][1] = sn;
+        if (apq != 0.0 && a2 > 1e-30 * sc2) jacobi_rotation(app, aqq, apq, c, sn);
+        cs[pb][0] = c; cs[pb][1] = sn;
+        cs[qb][0] = c; cs[qb][1] = sn;
       }
-      for (int b = blockIdx.x; b < kk / 2; b += nb) {
-        int p, q;
-        rr_pair(kk, r, b, p, q);
-        // rows p, q of A and of V^T, fetched together (kk <= 512: at most 4 per thread)
-        double vpr[4], vqr[4];
-        for (int x = threadIdx.x, u = 0; x < kk; x += blockDim.x, ++u) {
-          rp[x] = __ldcg(&A[(size_t)p * kk + x]);
-          rq[x] = __ldcg(&A[(size_t)q * kk + x]);
-          vpr[u] = __ldcg(&Vt[(size_t)p * kk + x]);
-          vqr[u] = __ldcg(&Vt[(size_t)q * kk + x]);
-        }
-        __syncthreads();
-        const double c = cs[p][0], sn = cs[p][1];
-        for (int x = threadIdx.x, u = 0; x < kk; x += blockDim.x, ++u) {
+#pragma unroll
+      for (int u = 0; u < kJacobiPer; ++u) {
+        const int x = threadIdx.x + u * kJacobiThreads;
+        if (x < kk) { rp[x] = ap[u]; rq[x] = aq[u]; }
+      }
+      __syncthreads();
+      const double c = cs[p][0], sn = cs[p][1];
+      // next round: partners of p and q, and the table copy it reads
+      const int r1 = r + 1 < kk - 1 ? r + 1 : 0, nxt = par ^ 1;
+      const int pn = rr_partner(kk, r1, p), qn = rr_partner(kk, r1, q);
+#pragma unroll
+      for (int u = 0; u < kJacobiPer; ++u) {
+        const int x = threadIdx.x + u * kJacobiThreads;
+        if (x < kk) {
           const int y = rr_partner(kk, r, x);
           const double c2 = cs[x][0], s2 = cs[x][1];
           const bool first = x < y;  // the smaller index is p of its pair
@@ -592,24 +633,18 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
           if (x == p) nq = 0.0;
           A[(size_t)p * kk + x] = np;
           A[(size_t)q * kk + x] = nq;
-          Vt[(size_t)p * kk + x] = c * vpr[u] - sn * vqr[u];
-          Vt[(size_t)q * kk + x] = sn * vpr[u] + c * vqr[u];
+          Vt[(size_t)p * kk + x] = c * vp[u] - sn * vq[u];
+          Vt[(size_t)q * kk + x] = sn * vp[u] + c * vq[u];
+          if (x == p) rdiag[nxt * kk + p] = np;
+          if (x == q) rdiag[nxt * kk + q] = nq;
+          if (x == pn && p < pn) roff[nxt * kk + p] = np;
+          if (x == qn && q < qn) roff[nxt * kk + q] = nq;
         }
-        __syncthreads();
       }
-      if (!grid_sync(gb, nb)) return;
+      par = nxt;
+      if (!grid_sync(gb, nb, epoch)) return;
     }
-    red[threadIdx.x] = my_off;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    const double off_max = red[0];
-    __syncthreads();
-    // quadratic convergence: once every off-diagonal met in a sweep is below 1e-8 of its
-    // diagonal scale, the rotations of that sweep leave them at rounding level
-    if (off_max < 1e-8) break;
+    if (!__syncthreads_or(unconv)) break;
   }
   // sort ascending (stable by index) and write theta, S (column i = eigenvector i)
   if (blockIdx.x == 0) {
@@ -628,7 +663,7 @@ __global__ void __launch_bounds__(128) jacobi_kernel(int k, int kk, const double
 
 size_t jacobi_work_doubles(int k) {
   const int kk = k + (k & 1);
-  return 2 * (size_t)kk * kk + 3 * (size_t)kk;
+  return 2 * (size_t)kk * kk + 4 * (size_t)kk;
 }
 
 int jacobi_eig(int k, const double *H, int ldh, double *theta, double *S, int lds, JacobiWork w, cudaStream_t st) {
@@ -638,15 +673,14 @@ int jacobi_eig(int k, const double *H, int ldh, double *theta, double *S, int ld
   int dev = 0, per_sm = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 128, 0);
-  int nb = kk / 2;
-  if (nb > per_sm * sms) nb = per_sm * sms;
-  if (nb < 1) return SLRF_ECUDA;
-  cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
+  const int nb = kk / 2;  // one block per rotation pair, all co-resident
+  if (per_sm < 1 || nb > per_sm * sms) return SLRF_ECUDA;
+  cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st);
   cudaMemsetAsync(w.err, 0, sizeof(int), st);
   int max_sweeps = 40;
   void *args[] = {&k, &kk, (void *)&H, &ldh, &theta, &S, &lds, &w, &max_sweeps};
-  cudaError_t e = cudaLaunchCooperativeKernel((void *)jacobi_kernel, dim3(nb), dim3(128), args, 0, st);
+  cudaError_t e = cudaLaunchCooperativeKernel((void *)jacobi_kernel, dim3(nb), dim3(kJacobiThreads), args, 0, st);
   return e == cudaSuccess ? SLRF_OK : SLRF_ECUDA;
 }
 

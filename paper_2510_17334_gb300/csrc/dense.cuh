@@ -43,7 +43,7 @@ void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cud
 struct JacobiWork {
   double *A;        // kk x kk
   double *Vt;       // kk x kk
-  double *rot;      // 3 * kk
+  double *rot;      // 4 * kk: diagonal and pair entries of the next round, two copies
   int *flags;       // [4]
   unsigned *bar;    // [2] barrier counters
   int *err;         // [1]

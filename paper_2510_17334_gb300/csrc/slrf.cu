@@ -929,7 +929,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
     const int kk = L + (L & 1) < 2 ? 2 : L + (L & 1);
     AL(ctx->jw.A, (size_t)kk * kk);
     AL(ctx->jw.Vt, (size_t)kk * kk);
-    AL(ctx->jw.rot, 3 * (size_t)kk);
+    AL(ctx->jw.rot, 4 * (size_t)kk);
     AL(ctx->jw.flags, 4);
     AL(ctx->jw.bar, 4);
     ctx->jw.err = ctx->iflags + 9;
