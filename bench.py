@@ -28,7 +28,7 @@ METRIC = "eigenpairs/s and shifted column-solves/s at resid≤1e-8; SpMM HBM GB/
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz
 # DRAM bytes (read + write) of one cocg_spmm_kernel<double> launch on the 41^3 workload at
 # 160 columns x 8 poles, from the ncu capture summarised in profiles/launches_q1_lap_41_fp64.md
-SPMM64_TRAFFIC_Q1_41 = 6032729344 + 2846729984
+SPMM64_TRAFFIC_Q1_41 = 5978269696 + 2815613952
 
 
 # Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
