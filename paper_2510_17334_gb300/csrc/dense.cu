@@ -9,7 +9,15 @@
 namespace slrf {
 
 // ------------------------------------------------------------------------------ real SpMM
-// One warp per row, each lane owns up to 4 columns (lane + 32 t) of a 128-column group.
+// One warp per row; each lane owns U columns (lane + 32 u) of a 32U-column group, U chosen
+// per call as ceil(k / 32) up to 8, so a block of k <= 256 columns is one group (no group
+// that is mostly padding).  A row's CSR chunk is read once per warp; its entries reach the
+// lanes from shared memory (FP64: one broadcast load of (a, b) and one of the column instead
+// of five register shuffles), and the gathered row's address is one 32 x 32 -> 64-bit
+// multiply-add.
+constexpr int kSpmmRows = 8;  // warps (rows) per block
+
+template <int U>
 __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t *__restrict__ rowptr,
                                                         const int32_t *__restrict__ col,
                                                         const double *__restrict__ valA,
@@ -18,11 +26,17 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
                                                         double *__restrict__ YA, double *__restrict__ YB,
                                                         int ldy, const int *run_if) {
   if (run_if != nullptr && *run_if == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (i >= n) return;
-  const int c0 = blockIdx.y * 128 + lane;
-  double sa[4] = {0, 0, 0, 0}, sb[4] = {0, 0, 0, 0};
+  __shared__ double2 s_ab[kSpmmRows][32];
+  __shared__ int s_c[kSpmmRows][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kSpmmRows + warp;
+  if (i >= n) return;  // warp-uniform; only warp-level synchronisation below
+  const int c0 = blockIdx.y * (32 * U) + lane;
+  const char *const xl = reinterpret_cast<const char *>(X + c0);
+  const unsigned row_bytes = (unsigned)ldx * (unsigned)sizeof(double);
+  double sa[U], sb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) { sa[u] = 0.0; sb[u] = 0.0; }
   const int64_t rs = rowptr[i], re = rowptr[i + 1];
   for (int64_t e0 = rs; e0 < re; e0 += 32) {
     const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
@@ -33,24 +47,27 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
       al = YA ? valA[e0 + lane] : 0.0;
       bl = YB ? valB[e0 + lane] : 0.0;
     }
+    __syncwarp();
+    s_ab[warp][lane] = make_double2(al, bl);
+    s_c[warp][lane] = cl;
+    __syncwarp();
+#pragma unroll 4
     for (int t = 0; t < cnt; ++t) {
-      const int c = __shfl_sync(0xffffffffu, cl, t);
-      const double a = __shfl_sync(0xffffffffu, al, t);
-      const double b = __shfl_sync(0xffffffffu, bl, t);
-      const double *xr = X + (size_t)c * ldx;
+      const int c = s_c[warp][t];
+      const double2 ab = s_ab[warp][t];
+      const double *xr = reinterpret_cast<const double *>(xl + (unsigned long long)(unsigned)c * row_bytes);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int cc = c0 + 32 * u;
-        if (cc < k) {
-          const double x = xr[cc];
-          if (YA) sa[u] = fma(a, x, sa[u]);
-          if (YB) sb[u] = fma(b, x, sb[u]);
+      for (int u = 0; u < U; ++u) {
+        if (c0 + 32 * u < k) {
+          const double x = xr[32 * u];
+          if (YA) sa[u] = fma(ab.x, x, sa[u]);
+          if (YB) sb[u] = fma(ab.y, x, sb[u]);
         }
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int cc = c0 + 32 * u;
     if (cc < k) {
       if (YA) YA[(size_t)i * ldy + cc] = sa[u];
@@ -59,26 +76,24 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
   }
 }
 
-void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
-               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st,
-               const int *run_if) {
-  if (n <= 0 || k <= 0) return;
-  dim3 grid((unsigned)((n + 7) / 8), (unsigned)((k + 127) / 128));
-  spmm_real_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy, run_if);
-}
-
 // YB = B X with FP32 products and sums (FP64 in and out): for the first Cholesky-QR pass,
-// whose Gram matrix is formed in FP32 anyway.  Same work split as spmm_real_kernel.
+// whose Gram matrix is formed in FP32 anyway.  Same work split as spmm_real_kernel; the
+// CSR chunk reaches the lanes by two 32-bit shuffles per entry.
+template <int U>
 __global__ void __launch_bounds__(256) spmm_b32_kernel(int64_t n, const int64_t *__restrict__ rowptr,
                                                        const int32_t *__restrict__ col,
                                                        const double *__restrict__ valB,
                                                        const double *__restrict__ X, int ldx, int k,
                                                        double *__restrict__ YB, int ldy) {
   const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t i = (int64_t)blockIdx.x * kSpmmRows + (threadIdx.x >> 5);
   if (i >= n) return;
-  const int c0 = blockIdx.y * 128 + lane;
-  float sb[4] = {0.f, 0.f, 0.f, 0.f};
+  const int c0 = blockIdx.y * (32 * U) + lane;
+  const char *const xl = reinterpret_cast<const char *>(X + c0);
+  const unsigned row_bytes = (unsigned)ldx * (unsigned)sizeof(double);
+  float sb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) sb[u] = 0.f;
   const int64_t rs = rowptr[i], re = rowptr[i + 1];
   for (int64_t e0 = rs; e0 < re; e0 += 32) {
     const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
@@ -92,26 +107,59 @@ __global__ void __launch_bounds__(256) spmm_b32_kernel(int64_t n, const int64_t 
     for (int t = 0; t < cnt; ++t) {
       const int c = __shfl_sync(0xffffffffu, cl, t);
       const float b = __shfl_sync(0xffffffffu, bl, t);
-      const double *xr = X + (size_t)c * ldx;
+      const double *xr = reinterpret_cast<const double *>(xl + (unsigned long long)(unsigned)c * row_bytes);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int cc = c0 + 32 * u;
-        if (cc < k) sb[u] = fmaf(b, (float)xr[cc], sb[u]);
-      }
+      for (int u = 0; u < U; ++u)
+        if (c0 + 32 * u < k) sb[u] = fmaf(b, (float)xr[32 * u], sb[u]);
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int cc = c0 + 32 * u;
     if (cc < k) YB[(size_t)i * ldy + cc] = (double)sb[u];
   }
 }
 
+static int spmm_lanes(int k) { return std::min(8, (k + 31) / 32); }
+
+void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st,
+               const int *run_if) {
+  if (n <= 0 || k <= 0) return;
+  const int U = spmm_lanes(k);
+  dim3 grid((unsigned)((n + kSpmmRows - 1) / kSpmmRows), (unsigned)((k + 32 * U - 1) / (32 * U)));
+#define SPMM_REAL(UU) \
+  spmm_real_kernel<UU><<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy, run_if)
+  switch (U) {
+    case 1: SPMM_REAL(1); break;
+    case 2: SPMM_REAL(2); break;
+    case 3: SPMM_REAL(3); break;
+    case 4: SPMM_REAL(4); break;
+    case 5: SPMM_REAL(5); break;
+    case 6: SPMM_REAL(6); break;
+    case 7: SPMM_REAL(7); break;
+    default: SPMM_REAL(8); break;
+  }
+#undef SPMM_REAL
+}
+
 void spmm_b32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valB, const double *X, int ldx,
               int k, double *YB, int ldy, cudaStream_t st) {
   if (n <= 0 || k <= 0) return;
-  dim3 grid((unsigned)((n + 7) / 8), (unsigned)((k + 127) / 128));
-  spmm_b32_kernel<<<grid, 256, 0, st>>>(n, rowptr, col, valB, X, ldx, k, YB, ldy);
+  const int U = spmm_lanes(k);
+  dim3 grid((unsigned)((n + kSpmmRows - 1) / kSpmmRows), (unsigned)((k + 32 * U - 1) / (32 * U)));
+#define SPMM_B32(UU) spmm_b32_kernel<UU><<<grid, 256, 0, st>>>(n, rowptr, col, valB, X, ldx, k, YB, ldy)
+  switch (U) {
+    case 1: SPMM_B32(1); break;
+    case 2: SPMM_B32(2); break;
+    case 3: SPMM_B32(3); break;
+    case 4: SPMM_B32(4); break;
+    case 5: SPMM_B32(5); break;
+    case 6: SPMM_B32(6); break;
+    case 7: SPMM_B32(7); break;
+    default: SPMM_B32(8); break;
+  }
+#undef SPMM_B32
 }
 
 __global__ void shifted_residual_kernel(int64_t n, int k, const double *AV, const double *BV, int ld,
