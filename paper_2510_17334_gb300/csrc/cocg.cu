@@ -23,12 +23,6 @@
 // them in a fixed order (deterministic) and updates the per-column scalars.
 #include "cocg.cuh"
 
-#ifndef SLRF_SPMM_ROW2
-#define SLRF_SPMM_ROW2 0
-#endif
-#ifndef SLRF_SPMM_PREFETCH
-#define SLRF_SPMM_PREFETCH 0
-#endif
 #ifndef SLRF_GATHER_UNROLL
 #define SLRF_GATHER_UNROLL 8
 #endif
@@ -481,34 +475,13 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
         qv = ldv<R>(a.q + off);
       }
     };
-#if SLRF_SPMM_ROW2
-    for (int64_t i = i0 + warp; i < i1; i += 2 * kWarps) {
-      const int64_t i2 = i + kWarps;
-      C sa[VEC], sb[VEC], sa2[VEC], sb2[VEC];
-      gather_row(i, sa, sb);
-      if (i2 < i1) gather_row(i2, sa2, sb2);
-      Vec<R> rv, pv, qv;
-      load_own(i, rv, pv, qv);
-      finish_row(i, sa, sb, rv, pv, qv);
-      if (i2 < i1) {
-        load_own(i2, rv, pv, qv);
-        finish_row(i2, sa2, sb2, rv, pv, qv);
-      }
-    }
-#else
     for (int64_t i = i0 + warp; i < i1; i += kWarps) {
       C sa[VEC], sb[VEC];
       Vec<R> rv, pv, qv;
-#if SLRF_SPMM_PREFETCH
-      load_own(i, rv, pv, qv);
-      gather_row(i, sa, sb);
-#else
       gather_row(i, sa, sb);
       load_own(i, rv, pv, qv);
-#endif
       finish_row(i, sa, sb, rv, pv, qv);
     }
-#endif
   }
   double out[NQ];
   int w;
