@@ -86,10 +86,11 @@ def workload(name: str, it_max: int | None):
     return wl, desc
 
 
-def clocks_start():
+def clocks_start(raw_path: str | None = None):
+    """Sample nvidia-smi clocks and throttle reasons every 200 ms until clocks_stop();
+    the raw samples also go to raw_path when one is given."""
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        f = open(raw_path or os.devnull, "w")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
@@ -183,6 +184,8 @@ def main():
     ap.add_argument("--it-max", type=int, default=None)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also write the raw nvidia-smi clock samples of the timed region to this file")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch64: also time the plain FP64 batched solve")
     ap.add_argument("--mixed-it-max", type=int, default=8,
@@ -239,7 +242,7 @@ def main():
             torch.cuda.synchronize()
 
         barrier()
-        cp, cf = clocks_start()
+        cp, cf = clocks_start(args.clocks_csv)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         stats = []
@@ -407,7 +410,7 @@ def batch_bench(args, rank, world, local):
                 "outer_iters_max": st["outer_iters"], "column_iterations": st["column_iterations"],
                 "kernel_launches": st["kernel_launches"], "it_max": it_max}, evs
 
-    cp, cf = clocks_start()
+    cp, cf = clocks_start(args.clocks_csv)
     prec = 1 if args.precision == 0 and not args.compare_fp64 else args.precision
     main, evs_main = run(1, args.mixed_it_max if args.it_max is None else args.it_max)
     clk = clocks_stop(cp, cf, local)
@@ -469,7 +472,7 @@ def sens_bench(args, rank, world, local):
         torch.cuda.synchronize()
         return ctx, rc, nf, ev, X, rs, st, e0.elapsed_time(e1)
 
-    cp, cf = clocks_start()
+    cp, cf = clocks_start(args.clocks_csv)
     ctx, rc, nf, ev, X, rs, st, ms_solve = solve(P0.valA, V0)
     assert rc == 0 and nf == cnt, (rc, nf, cnt)
     cd = torch.from_numpy(cvec).cuda()
