@@ -93,7 +93,7 @@ class CocgInfo:
 
 
 def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarray,
-         it_max: int, tol: float):
+         it_max: int, tol: float, d: np.ndarray | None = None):
     """Conjugate orthogonal CG for the complex-symmetric M = A - sigma B, one RHS per column.
 
     ``sigma`` is a scalar or one shift per column (columns are independent systems).
@@ -107,14 +107,24 @@ def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarra
     (A - sigma B) u = (A - theta B) v solved from u0 = 0 (Sec. 4, Proposition (i)); with
     y0 = 0 it is the usual ||r||/||b||.
     A column whose mu or rho vanishes (or is not finite) stops and is flagged.
+
+    Jacobi preconditioning (reading R18; the paper preconditions its inner solver, Sec. 3.2):
+    with ``d`` (the positive diagonal of D) the same iteration runs on the symmetrically
+    scaled system  (D^-1/2 M D^-1/2) z = D^-1/2 b  from z0 = D^1/2 y0, and y = D^-1/2 z.
+    The scaled matrix is still complex symmetric, so COCG applies unchanged; residuals,
+    the stopping test and the returned relres are those of the scaled system.  d = None
+    is the unpreconditioned method (the scale is exactly 1).
     """
     sig = np.broadcast_to(np.asarray(sigma, dtype=np.complex128), (b.shape[1],))
+    s = np.ones(b.shape[0]) if d is None else 1.0 / np.sqrt(np.asarray(d, dtype=np.float64))
+    s = s[:, None]
 
     def M(X):
-        return (A @ X) - (B @ X) * sig[None, :]
+        # D^-1/2 (A - sigma B) D^-1/2 X
+        return s * ((A @ (s * X)) - (B @ (s * X)) * sig[None, :])
 
-    y = y0.astype(np.complex128, copy=True)
-    r = b.astype(np.complex128) - M(y)
+    y = y0.astype(np.complex128, copy=True) / s  # z0 = D^1/2 y0 (the loop works on z)
+    r = s * b.astype(np.complex128) - M(y)
     rn = np.linalg.norm(r, axis=0)
     bn = rn.copy()  # ||r0||
     active = rn > 0
@@ -144,7 +154,7 @@ def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarra
         rho = rho_new
         p = r + beta[None, :] * p
     relres = np.where(bn > 0, rn / np.where(bn > 0, bn, 1), 0.0)  # ||r|| / ||r0||
-    return y, CocgInfo(iters, relres, brk)
+    return s * y, CocgInfo(iters, relres, brk)  # y = D^-1/2 z
 
 
 # ----------------------------------------------------------------------------------------
@@ -157,12 +167,13 @@ class FilterInfo:
     breakdown: np.ndarray  # (m, k)
 
 
-def filter_apply(A, B, V, theta, sigma, w, it_max, tol):
+def filter_apply(A, B, V, theta, sigma, w, it_max, tol, d=None):
     """Apply the rational filter to the real block V (n x k), the filter step of Alg. 2.
 
     ``theta`` = None gives the zero initial guess; otherwise column c starts from
     y0 = v_c / (theta_c - sigma_j) (the warm start of Alg. 2).  All m x k systems are solved
     side by side as independent columns, pole-major: column j*k + c is pole j, vector c.
+    ``d``: diagonal of the Jacobi preconditioner of every shifted system (None: none).
     """
     n, k = V.shape
     m = len(sigma)
@@ -174,7 +185,7 @@ def filter_apply(A, B, V, theta, sigma, w, it_max, tol):
     else:
         th = np.tile(np.asarray(theta, dtype=np.float64), m)
         y0 = np.tile(V, (1, m)) / (th[None, :] - sig_cols[None, :])
-    Y, info = cocg(A, B, sig_cols, bb, y0, it_max, tol)
+    Y, info = cocg(A, B, sig_cols, bb, y0, it_max, tol, d)
     U = np.zeros((n, k))
     for j in range(m):
         U += 2.0 * np.real(w[j] * Y[:, j * k:(j + 1) * k])
@@ -254,14 +265,16 @@ class SolveResult:
 
 
 def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, outer_max=100,
-                  alpha=1.0, beta=0.01, lock=True, warm=True, poles=None, keep_trace=False):
+                  alpha=1.0, beta=0.01, lock=True, warm=True, poles=None, keep_trace=False, precond=False):
     """Enhanced ParaSLRF, Alg. 2, on one address space.
 
     Returns the locked eigenpairs sorted ascending.  ``lock`` = False / ``warm`` = False
-    give the basic method of Alg. 1 (no locking, zero initial guesses).
+    give the basic method of Alg. 1 (no locking, zero initial guesses).  ``precond`` = True
+    solves every shifted system with the Jacobi preconditioner D = diag(A) (see ``cocg``).
     """
     A = sp.csr_matrix(A)
     B = sp.csr_matrix(B)
+    d = A.diagonal() if precond else None
     n, L = V1.shape
     sigma, w = slrf_poles(m, gamma, alpha, beta) if poles is None else poles
     V = np.array(V1, dtype=np.float64)
@@ -275,7 +288,7 @@ def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, o
     status = E_NOCONV
     k = 0
     for k in range(1, outer_max + 1):
-        U, finfo = filter_apply(A, B, V, theta if warm else None, sigma, w, it_max, tol_in)
+        U, finfo = filter_apply(A, B, V, theta if warm else None, sigma, w, it_max, tol_in, d)
         if X.shape[1] > 0:
             U = b_orth(U, X, BX)
         U, st = cholqr2(U, B)

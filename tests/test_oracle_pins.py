@@ -57,13 +57,20 @@ def test_pole_weights_solve_the_regularised_fit():
 
 
 def test_filter_shape():
-    """Phi passes (0, gamma] and damps [1.3 gamma, inf): the filter property of Sec. 2."""
+    """Phi passes (0, gamma] and damps [1.3 gamma, inf): the filter property of Sec. 2.
+    The design (reading R1, m = 8, alpha = 1, beta = 0.01) has, on the normalised axis,
+    min Phi = 0.8711 (at t = gamma), max Phi = 1.0400 (at t = 0.832 gamma) on (0, gamma],
+    max |Phi| = 0.2233 beyond 1.3 gamma (at the band edge) and 0.0885 beyond 1.4 gamma."""
     g = 4150.528
     s, w = orc.slrf_poles(8, g)
-    inside = orc.filter_value(np.linspace(1e-3, 1, 500) * g, s, w)
-    outside = orc.filter_value(np.geomspace(1.3, 1e4, 500) * g, s, w)
-    assert inside.min() > 0.8 and inside.max() < 1.1
-    assert np.abs(outside).max() < 0.25
+    t_in = np.linspace(0, 1, 200001)[1:]
+    inside = orc.filter_value(t_in * g, s, w)
+    outside = orc.filter_value(np.geomspace(1.3, 1e4, 200001) * g, s, w)
+    beyond = orc.filter_value(np.geomspace(1.4, 1e4, 200001) * g, s, w)
+    assert abs(inside.min() - 0.8711) <= 1e-3 and t_in[np.argmin(inside)] == 1.0
+    assert abs(inside.max() - 1.0400) <= 1e-3
+    assert abs(np.abs(outside).max() - 0.2233) <= 1e-3 and np.argmax(np.abs(outside)) == 0
+    assert abs(np.abs(beyond).max() - 0.0885) <= 1e-3
     # the conjugate half: w/(t - s) + conj(w)/(t - conj s) = 2 Re(w/(t - s))
     t = 0.37 * g
     full = np.sum(w / (t - s) + np.conj(w) / (t - np.conj(s)))
@@ -129,6 +136,65 @@ def test_proposition_initial_residual_and_krylov_space():
         assert np.allclose(u, v + (sig - theta) * y, rtol=1e-9, atol=1e-10 * np.abs(u).max())
 
 
+def _galerkin_iterate(M, r0, k):
+    """The k-th COCG correction characterised without its recurrence: the vector c of
+    K_k(M, r0) whose residual r0 - M c is orthogonal to K_k in the unconjugated bilinear
+    form x^T y (Petrov-Galerkin condition of COCG).  Q spans K_k (any basis of it gives the
+    same c, since Q^T r = 0 <=> V^T r = 0 for V = Q T)."""
+    V = [r0]
+    for _ in range(k - 1):
+        V.append(M @ V[-1])
+    Q, _ = np.linalg.qr(np.stack(V, axis=1))
+    return Q @ np.linalg.solve(Q.T @ (M @ Q), Q.T @ r0)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_cocg_iterates_satisfy_the_galerkin_condition(precond):
+    """COCG (and its Jacobi-preconditioned form, reading R18) after k steps equals the
+    Petrov-Galerkin iterate of the (scaled) system in the Krylov space of its initial
+    residual, from a nonzero initial guess.  Preconditioned: the system is
+    D^-1/2 (A - sigma B) D^-1/2 z = D^-1/2 b with D = diag(A), z = D^1/2 y."""
+    E = np.exp(np.random.default_rng(21).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    A, B = p.A(), p.B()
+    Ad, Bd = A.toarray(), B.toarray()
+    rng = np.random.default_rng(22)
+    b = rng.standard_normal((p.n, 1))
+    y0 = rng.standard_normal((p.n, 1)) * 1e-3
+    sig = 40.0 * (1 + 1j)
+    d = Ad.diagonal() if precond else np.ones(p.n)
+    h = 1.0 / np.sqrt(d)
+    Mh = h[:, None] * (Ad - sig * Bd) * h[None, :]
+    z0 = y0[:, 0] / h
+    r0 = h * (b[:, 0] - (Ad - sig * Bd) @ y0[:, 0])
+    for k in (1, 2, 4, 6):
+        y, info = orc.cocg(A, B, sig, b, y0, k, 0.0, Ad.diagonal() if precond else None)
+        ref = h * (z0 + _galerkin_iterate(Mh, r0, k))
+        assert info.iters[0] == k
+        assert np.abs(y[:, 0] - ref).max() <= 1e-9 * np.abs(ref).max(), k
+        # relres is the scaled system's ||r|| / ||r0||
+        rk = h * (b[:, 0] - (Ad - sig * Bd) @ y[:, 0])
+        assert abs(info.relres[0] - np.linalg.norm(rk) / np.linalg.norm(r0)) <= 1e-8 * info.relres[0]
+
+
+def test_preconditioned_cocg_solves_the_unscaled_system():
+    """Converged preconditioned COCG equals a dense complex solve of (A - sigma B) y = b,
+    and a constant diagonal (D = c I) gives the unpreconditioned iterates."""
+    E = np.exp(np.random.default_rng(23).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    A, B = p.A(), p.B()
+    rng = np.random.default_rng(24)
+    b = rng.standard_normal((p.n, 2))
+    sig = 25.0 * (1 + 1j)
+    ref = np.linalg.solve(A.toarray() - sig * B.toarray(), b)
+    y, info = orc.cocg(A, B, sig, b, np.zeros((p.n, 2)), 2000, 1e-13, A.diagonal())
+    assert np.abs(y - ref).max() <= 1e-9 * np.abs(ref).max() and not info.breakdown.any()
+    y1, i1 = orc.cocg(A, B, sig, b, np.zeros((p.n, 2)), 7, 0.0)
+    y2, i2 = orc.cocg(A, B, sig, b, np.zeros((p.n, 2)), 7, 0.0, np.full(p.n, 4.0))
+    assert np.abs(y1 - y2).max() <= 1e-12 * np.abs(y1).max()
+    assert np.allclose(i1.relres, i2.relres, rtol=1e-10)
+
+
 # ---------------------------------------------------------------- a5: the filter on eigenvectors
 def test_filter_apply_on_exact_eigenvectors():
     """With X exact eigenvectors and converged solves, filter_apply(X) = X diag(Phi(lambda))."""
@@ -168,6 +234,46 @@ def test_borth_cholqr2_rayleigh_ritz():
     assert np.abs(V.T @ Bd @ V - np.eye(8)).max() <= 1e-12
     res, res_paper, _ = orc.ritz_residuals(A, B, V, th)
     assert res.max() <= 1e-10 and res_paper.max() <= 1e-10
+
+
+def test_ritz_residuals_closed_form():
+    """v = x_i + eps x_j with B-orthonormal eigenvectors x (A x = l B x) and b = B x:
+    A v = l_i b_i + eps l_j b_j, B v = b_i + eps b_j, and at theta = the Rayleigh quotient
+    (l_i + eps^2 l_j) / (1 + eps^2):
+      ||A v - theta B v||^2 = (l_i - th)^2 |b_i|^2 + 2 eps (l_i - th)(l_j - th) b_i.b_j
+                              + eps^2 (l_j - th)^2 |b_j|^2,
+      ||A v||^2 = l_i^2 |b_i|^2 + 2 eps l_i l_j b_i.b_j + eps^2 l_j^2 |b_j|^2,
+      ||v||_B^2 = 1 + eps^2.
+    The relative residual is the first over the second; the paper's form (Sec. 3.2) is
+    ||A v - theta B v|| / (theta ||v||_B)."""
+    p, A, B = _small_q1((6, 5, 4))
+    lam, Xe = sla.eigh(A.toarray(), B.toarray())
+    cases = [(3, 7, 0.3), (10, 2, 0.05), (20, 21, 1e-2), (0, 40, 0.5)]
+    V = np.stack([Xe[:, i] + e * Xe[:, j] for i, j, e in cases], axis=1)
+    th = np.array([(lam[i] + e * e * lam[j]) / (1 + e * e) for i, j, e in cases])
+    res, res_paper, BV = orc.ritz_residuals(A, B, V, th)
+    assert np.abs(BV - B @ V).max() <= 1e-14 * np.abs(B @ V).max()
+    for c, (i, j, e) in enumerate(cases):
+        bi, bj = B @ Xe[:, i], B @ Xe[:, j]
+        li, lj, t = lam[i], lam[j], th[c]
+        num = (li - t) ** 2 * (bi @ bi) + 2 * e * (li - t) * (lj - t) * (bi @ bj) + e * e * (lj - t) ** 2 * (bj @ bj)
+        den = li * li * (bi @ bi) + 2 * e * li * lj * (bi @ bj) + e * e * lj * lj * (bj @ bj)
+        assert abs(res[c] - np.sqrt(num / den)) <= 1e-9 * res[c], (c, res[c], np.sqrt(num / den))
+        paper = np.sqrt(num) / (t * np.sqrt(1 + e * e))
+        assert abs(res_paper[c] - paper) <= 1e-9 * paper
+
+
+def test_sign_normalise():
+    """Reading R11: each vector's entry of largest magnitude is made positive; among equal
+    magnitudes the first one decides; a zero vector stays zero."""
+    V = np.array([[1.0, 2.0, 0.0, -0.5],
+                  [-3.0, -2.0, 0.0, 0.25],
+                  [2.0, 1.0, 0.0, 0.5]])
+    out = orc.sign_normalise(V)
+    expect = np.array([[-1.0, 2.0, 0.0, 0.5],
+                       [3.0, -2.0, 0.0, -0.25],
+                       [-2.0, 1.0, 0.0, -0.5]])
+    assert np.array_equal(out, expect)
 
 
 def test_cholqr2_reports_a_non_spd_gram():
@@ -251,7 +357,21 @@ def test_stop_rule_needs_a_resolved_subspace():
     r = orc.enhanced_slrf(A, B, gamma, V1, it_max=5, outer_max=60)
     assert r.status == orc.OK and len(r.evals) == cnt
     assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-10
-    assert r.outer_iters == 33
+
+
+def test_preconditioned_solve_against_dense_eigh():
+    """Alg. 2 with Jacobi-preconditioned inner solves (reading R18) returns the same
+    eigenpairs: the preconditioner changes how fast, not what, the method converges to."""
+    E = np.exp(np.random.default_rng(9).normal(0, 0.5, 3 * 3 * 2))
+    p = si.q1_elasticity((4, 4, 3), E=E)
+    A, B = p.A(), p.B()
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    gamma, cnt = pins.gap_gamma(lam, 10)
+    V1 = si.start_block(p.n, int(np.ceil(1.5 * cnt)), 6)
+    r = orc.enhanced_slrf(A, B, gamma, V1, m=8, it_max=20, outer_max=40, precond=True)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
+    assert r.resid.max() <= 1e-8
 
 
 def test_basic_method_agrees():
