@@ -84,6 +84,16 @@ typedef struct {
                              consecutive outer steps whose lowest active Ritz pair is still
                              unresolved (relative residual > 1e-2); 0 = fixed It_max (the
                              paper's It_max-linear); default 0                               */
+  int precond;            /* 1 = Jacobi-preconditioned inner solves: D = diag(A) applied as the
+                             symmetric scaling D^-1/2 (A - sigma_j B) D^-1/2 (complex symmetric,
+                             so COCG applies unchanged; the paper preconditions its inner
+                             solver, Sec. 3.2); the inner stopping test then uses the scaled
+                             residual.  A must have a positive diagonal.  0 = none; default 0 */
+  int group;              /* rows per group of the COCG SpMM's grouped-row format (rows of a
+                             group share one union column list, so each gathered row feeds
+                             all of them): 0 = choose (timed when autotune = 1, else from a
+                             cost model of the pattern), 1 = plain CSR, 2..4 = that many;
+                             default 0 */
 } slrf_opts;
 
 /* Statistics of the last slrf_solve (host struct filled by the library). */
@@ -104,8 +114,8 @@ typedef struct {
 /* Fill *opts with the paper's defaults: m = 8, alpha = 1, beta = 0.01 (Sec. 3.2),
  * band = 1.3, it_max = 40, refine_max = 1, outer_max = 100, tol_inner = 1e-10 (Sec. 3.2),
  * tol_eig = 1e-8 (Sec. 3.2), precision = 0, warm_start = 1, lock = 1 (Sec. 4), use_graph = 1,
- * nev = 0, seed = 1, poles = weights = NULL, autotune = 0, dense = 1, it_adapt = 0.  Returns
- * SLRF_EINVAL if opts is NULL. */
+ * nev = 0, seed = 1, poles = weights = NULL, autotune = 0, dense = 1, it_adapt = 0, precond = 0,
+ * group = 0.  Returns SLRF_EINVAL if opts is NULL. */
 int slrf_opts_default(slrf_opts *opts);
 
 /* Create a solver context for the pencil (A, B), the interval (0, gamma] and search-block
@@ -113,8 +123,10 @@ int slrf_opts_default(slrf_opts *opts);
  * Copies the pattern and both value arrays into library storage, designs (or copies) the
  * pole/weight table {sigma_j, w_j} (Sec. 2.2) and allocates the whole working set for L
  * columns, so that no later call allocates.  stream is a cudaStream_t or NULL.
- * Errors: SLRF_EINVAL (NULL pointers, n < 1, gamma <= 0, L < 1 or L > n, m outside 1..32),
- * SLRF_ENOMEM (working set does not fit), SLRF_ECUDA.  On error *ctx is set to NULL. */
+ * Errors: SLRF_EINVAL (NULL pointers, n < 1, gamma <= 0, L < 1 or L > n, m outside 1..32,
+ * a malformed CSR pattern, precond = 1 with a non-positive or missing diagonal entry of A,
+ * group outside 0..4), SLRF_ENOMEM (working set does not fit), SLRF_ECUDA.  On error *ctx is
+ * set to NULL. */
 int slrf_setup(slrf_ctx **ctx, const slrf_csr_pair *pencil, double gamma, int block_L,
                const slrf_opts *opts, void *stream);
 
@@ -246,14 +258,18 @@ int slrf_eig_grad(slrf_ctx *ctx, int k, const double *evals, const double *X, in
  * whose working set -- about 64 n W + 24 n k bytes, W = k m rounded up to a multiple of
  * 32 -- does not fit returns SLRF_EINVAL before any device work (the 1D bar with
  * n = 2000, k = 32, m = 8 uses 36 MB).  The call makes no cudaMalloc, cudaFree or other
- * allocating call.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture.  The array keeps the previous call's contents and the call clears
+ * allocating call.  Every call looks up the array's device address with
+ * cudaGetSymbolAddress on the current device (a query, no allocation).  Before any kernel
+ * gathers through the pattern, the call checks it on the device (rowptr non-decreasing
+ * from 0 to nnz, columns in [0, n)) and refuses a malformed one.  A designed pole table
+ * stays in the array and is reused by the next call on the device with the same m, gamma,
+ * alpha, beta and band.  The array keeps the previous call's contents and the call clears
  * what must start at zero; every call shares the one array, so calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialised by the
- * caller.  Synchronises the stream once, after setting up the pole table.
- * Errors: SLRF_EINVAL (NULL or inconsistent arguments, precision != 0, too large),
- * SLRF_ECUDA. */
+ * caller.  Synchronises the stream once (to read the pattern check and the pole-design
+ * status back), so a call cannot be captured into a CUDA graph.
+ * Errors: SLRF_EINVAL (NULL or inconsistent arguments, n > INT32_MAX, a malformed CSR
+ * pattern, precision != 0, precond != 0, too large), SLRF_ECUDA. */
 int slrf_filter_apply_static(const slrf_csr_pair *pencil, double gamma, const slrf_opts *opts,
                              const double *X, int k, const double *theta, double *U, void *stream);
 

@@ -34,8 +34,16 @@
 #ifndef SLRF_SPMM_SREC32
 #define SLRF_SPMM_SREC32 0
 #endif
+// grouped-row SpMM: records in flight per warp, resident blocks per SM
+#ifndef SLRF_GRP_UNROLL
+#define SLRF_GRP_UNROLL 4
+#endif
+#ifndef SLRF_GRP_MINB
+#define SLRF_GRP_MINB 2
+#endif
 namespace slrf {
 constexpr int kGatherUnroll = SLRF_GATHER_UNROLL;  // CSR entries of a row in flight per warp
+constexpr int kGrpUnroll = SLRF_GRP_UNROLL;        // grouped records in flight per warp
 }
 
 namespace slrf {
@@ -293,6 +301,8 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         }
         part[v] = 2.0 * (wt[v].x * yr - wt[v].y * yi);
       }
+      // preconditioned solves work on z = D^1/2 y: y = dsc_i z
+      const double ds = a.dsc != nullptr ? a.dsc[i] : 1.0;
       if (a.mp >= VEC) {
         double s = 0.0;
 #pragma unroll
@@ -301,15 +311,18 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         const int c = w0 / a.mp;
         if ((lane % lanes_per_col) == 0 && c < a.k) {
           if (a.gscale != nullptr) s /= a.gscale[c];
+          if (a.dsc != nullptr) s *= ds;
           a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
         }
       } else {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const int c = (w0 + v) / a.mp;
-          if (c < a.k)
-            a.U[(size_t)i * a.ldu + c] =
-                a.coefV[c] * a.V[(size_t)i * a.ldv + c] + (a.gscale ? part[v] / a.gscale[c] : part[v]);
+          if (c < a.k) {
+            double s = a.gscale ? part[v] / a.gscale[c] : part[v];
+            if (a.dsc != nullptr) s *= ds;
+            a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
+          }
         }
       }
     }
@@ -372,6 +385,37 @@ template <> __device__ __forceinline__ void srec_get<double>(const SRec<double> 
   c = r[t].c;
   av = ab.x;
   bv = ab.y;
+}
+
+// Block and grid reduction of the mu partials of one SpMM launch, then alpha = rho / mu per
+// (pole, column) in the last block of the tile (breakdown: mu = 0 or not finite).
+template <typename R, int VEC>
+__device__ __forceinline__ void spmm_tail(const CocgArgs<R> &a, const R (&acc)[VEC][2], const int w_tile0,
+                                          const int rb, const int tile) {
+  constexpr int NQ = 2;
+  double out[NQ];
+  int w;
+  double accd[VEC][NQ];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
+  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+    return;
+  if (threadIdx.x < 32 * VEC) {
+    WScal s = a.ws[w];
+    if (s.active) {
+      const double2 mu = make_double2(out[0], out[1]);
+      if (!cfinite(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
+        s.active = 0;
+        s.brk = 1;
+        s.alpha = make_double2(0.0, 0.0);
+      } else {
+        s.alpha = cdiv(s.rho, mu);
+      }
+      a.ws[w] = s;
+    }
+  }
 }
 
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
@@ -483,29 +527,190 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
       finish_row(i, sa, sb, rv, pv, qv);
     }
   }
-  double out[NQ];
-  int w;
-  double accd[VEC][NQ];
+  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile);
+}
+
+// s = (A - sigma B) r for groups of G consecutive rows that share one union column list
+// (grouped-row format, see CocgArgs): every gathered row of r feeds all G rows, so a row
+// costs union/G gathers instead of its own count (a 3-dof elasticity node: 27 instead of
+// 81).  Each warp walks its groups chunk by chunk (kGrpChunk records); lane 0 stages the
+// next chunk but one into the warp's other shared-memory buffer with a 1-D bulk copy, so
+// the records arrive through the TMA engine while the lanes gather and multiply.  All
+// lanes read a record with broadcast loads.  FP32: the complex products are packed FP32
+// FMAs on (a, a) x (re, im).  Waits are bounded (2 s, then *err and a drain of the
+// outstanding copies).
+template <typename R, int G, bool FRESH>
+__device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const int rb, const int tile) {
+  constexpr int VEC = cocg_vec<R>();
+  constexpr int RS = grec_bytes<G>();
+  constexpr int CH = kGrpChunk;
+  using C = cx_t<R>;
+  extern __shared__ __align__(128) unsigned char grp_smem[];
+  __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w_tile0 = tile * 32 * VEC;
+  const int w0 = w_tile0 + lane * VEC;
+  unsigned char *const sbuf = grp_smem + (size_t)warp * 2 * CH * RS;
+  uint64_t *const bar = s_bar[warp];
+  C sg[VEC], be[VEC];
+  bool any_act = false;
 #pragma unroll
-  for (int v = 0; v < VEC; ++v)
+  for (int v = 0; v < VEC; ++v) {
+    const WScal &s = a.ws[w0 + v];
+    any_act |= s.active != 0;
+    be[v] = to_c<R>(s.beta);
+    sg[v] = a.sig[(w0 + v) & (a.mp - 1)];
+  }
+  const bool warp_act = __any_sync(0xffffffffu, any_act);
+  R acc[VEC][2];
 #pragma unroll
-    for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
-  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
-    return;
-  if (threadIdx.x < 32 * VEC) {
-    WScal s = a.ws[w];
-    if (s.active) {
-      const double2 mu = make_double2(out[0], out[1]);
-      if (!cfinite(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
-        s.active = 0;
-        s.brk = 1;
-        s.alpha = make_double2(0.0, 0.0);
-      } else {
-        s.alpha = cdiv(s.rho, mu);
+  for (int v = 0; v < VEC; ++v) acc[v][0] = acc[v][1] = R(0);
+  const int gpb = a.rows_per_block / G;  // groups per row block (rows_per_block is a multiple of G)
+  const int64_t gb0 = (int64_t)rb * gpb;
+  const int64_t gb1 = (gb0 + gpb < a.ngroups ? gb0 + gpb : a.ngroups);
+  if (warp_act && gb0 + warp < gb1) {
+    if (lane == 0) {
+      mbar_init(bar, 1);
+      mbar_init(bar + 1, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const char *const rlane = reinterpret_cast<const char *>(a.r + w0);
+    const unsigned wbytes = (unsigned)a.W * (unsigned)sizeof(C);
+    // work items (group, chunk) of this warp: groups gb0 + warp, + kWarps, ...
+    auto nchunks = [&](int64_t g) -> int {
+      const int64_t c = a.gptr[g + 1] - a.gptr[g];
+      return c <= 0 ? 1 : (int)((c + CH - 1) / CH);
+    };
+    auto first = [&](int64_t g, int c, int &cnt) -> int64_t {
+      const int64_t e0 = a.gptr[g] + (int64_t)c * CH, e1 = a.gptr[g + 1];
+      cnt = (int)(e1 - e0 < CH ? e1 - e0 : CH);
+      if (cnt < 0) cnt = 0;
+      return e0;
+    };
+    auto issue = [&](int b, int64_t g, int c) {
+      if (lane == 0) {
+        int cnt;
+        const int64_t e0 = first(g, c, cnt);
+        // the lanes' shared-memory reads of this buffer (ordered by the __syncwarp before
+        // the call) precede the asynchronous proxy's writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (cnt > 0) {
+          mbar_expect_tx(bar + b, (uint32_t)(cnt * RS));
+          bulk_g2s(sbuf + (size_t)b * CH * RS, a.grec + (size_t)e0 * RS, (uint32_t)(cnt * RS), bar + b);
+        } else {
+          mbar_arrive(bar + b);
+        }
       }
-      a.ws[w] = s;
+    };
+    int64_t cg = gb0 + warp, ng = cg;  // current item, next item
+    int cc = 0, nc = 0;
+    auto advance = [&](int64_t &g, int &c) {
+      if (c + 1 < nchunks(g)) ++c;
+      else { g += kWarps; c = 0; }
+    };
+    issue(0, cg, cc);
+    advance(ng, nc);
+    if (ng < gb1) issue(1, ng, nc);
+    uint32_t ph0 = 0, ph1 = 0;
+    int b = 0;
+    bool failed = false;
+    C sa[G][VEC], sb[G][VEC];
+#pragma unroll
+    for (int j = 0; j < G; ++j)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
+    while (cg < gb1) {
+      if (!mbar_wait(bar + b, b ? ph1 : ph0, a.err, 1)) { failed = true; break; }
+      if (b) ph1 ^= 1u; else ph0 ^= 1u;
+      int cnt;
+      first(cg, cc, cnt);
+      const unsigned char *rb_ = sbuf + (size_t)b * CH * RS;
+#pragma unroll kGrpUnroll
+      for (int t = 0; t < cnt; ++t) {
+        const unsigned char *rp = rb_ + t * RS;
+        const int c = *reinterpret_cast<const int *>(rp + 16 * G);
+        const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            const float2 av = *reinterpret_cast<const float2 *>(rp + 8 * j);
+            const float2 bv = *reinterpret_cast<const float2 *>(rp + 8 * (G + j));
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              sa[j][v] = ffma2(av, x.z[v], sa[j][v]);
+              sb[j][v] = ffma2(bv, x.z[v], sb[j][v]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            const double av = *reinterpret_cast<const double *>(rp + 8 * j);
+            const double bv = *reinterpret_cast<const double *>(rp + 8 * (G + j));
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              sa[j][v].x = fma(av, x.z[v].x, sa[j][v].x);
+              sa[j][v].y = fma(av, x.z[v].y, sa[j][v].y);
+              sb[j][v].x = fma(bv, x.z[v].x, sb[j][v].x);
+              sb[j][v].y = fma(bv, x.z[v].y, sb[j][v].y);
+            }
+          }
+        }
+      }
+      if (cc + 1 >= nchunks(cg)) {
+        // last chunk of the group: p = r + beta p, q = s + beta q for its rows, mu partials
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int64_t i = cg * G + j;
+          if (i < a.n) {
+            const size_t off = (size_t)i * a.W + w0;
+            const Vec<R> rv = ldv<R>(a.r + off);
+            Vec<R> pv, qv;
+            if (!FRESH) {
+              pv = ldv<R>(a.p + off);
+              qv = ldv<R>(a.q + off);
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              const C sv = cfms(sg[v], sb[j][v], sa[j][v]);  // A r - sigma B r
+              const C pn = FRESH ? rv.z[v] : cfma(be[v], pv.z[v], rv.z[v]);
+              const C qn = FRESH ? sv : cfma(be[v], qv.z[v], sv);
+              pv.z[v] = pn;
+              qv.z[v] = qn;
+              acc[v][0] += pn.x * qn.x - pn.y * qn.y;
+              acc[v][1] += pn.x * qn.y + pn.y * qn.x;
+            }
+            stv<R>(a.p + off, pv);
+            stv<R>(a.q + off, qv);
+          }
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
+        }
+      }
+      __syncwarp();
+      // stage the item after next into the buffer just read
+      int64_t g2 = ng;
+      int c2 = nc;
+      if (g2 < gb1) {
+        advance(g2, c2);
+        if (g2 < gb1) issue(b, g2, c2);
+      }
+      cg = ng;
+      cc = nc;
+      ng = g2;
+      nc = c2;
+      b ^= 1;
+    }
+    if (failed) {
+      // wait (bounded) for the copies this warp may still have in flight, then leave
+      if (lane == 0) {
+        mbar_wait(bar + b, b ? ph1 : ph0, a.err, 1);
+        if (ng < gb1) mbar_wait(bar + (b ^ 1), b ? ph0 : ph1, a.err, 1);
+      }
+      __syncwarp();
     }
   }
+  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile);
 }
 
 // ------------------------------------------------------------------------------ residual
@@ -623,9 +828,13 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(c
 // so the two run side by side: the SpMM is bound by the FP64 pipe (or by the gather path
 // in FP32), the update by HBM.  Blocks alternate between the two kinds so that both are
 // resident from the start; within each kind the row block varies fastest.
-template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(const CocgArgs<R> a, int s0, int ns,
-                                                                              int u0, int nu) {
+// resident blocks per SM of the grouped SpMM (more registers: G rows of accumulators)
+template <typename R, int G> __host__ __device__ constexpr int cocg_grp_minb() {
+  return G == 1 ? cocg_minb<R>() : SLRF_GRP_MINB;
+}
+template <typename R, bool FIRST, int FM, int G>
+__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, G>())) cocg_dual_kernel(const CocgArgs<R> a, int s0,
+                                                                                       int ns, int u0, int nu) {
   const int NS = a.nrb * ns, NU = a.nrb * nu;
   const int both = 2 * (NS < NU ? NS : NU);
   const int b = blockIdx.x;
@@ -638,12 +847,20 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(con
     spmm = NS > NU;
     item = (b - both) + (NS < NU ? NS : NU);
   }
-  if (spmm) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
-  else cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
+  if (spmm) {
+    if constexpr (G == 1) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
+    else cocg_spmm_grp_body<R, G, false>(a, item % a.nrb, s0 + item / a.nrb);
+  } else {
+    cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
+  }
 }
 template <typename R, bool FRESH>
 __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_kernel(const CocgArgs<R> a) {
   cocg_spmm_body<R, FRESH>(a, blockIdx.x, blockIdx.y);
+}
+template <typename R, int G, bool FRESH>
+__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, G>())) cocg_spmm_grp_kernel(const CocgArgs<R> a) {
+  cocg_spmm_grp_body<R, G, FRESH>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
@@ -688,6 +905,95 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_residual_batched(const CocgA
   SLRF_BATCH_LOOP((cocg_residual_body<R>(a, local % a.nrb, local / a.nrb)))
 }
 #undef SLRF_BATCH_LOOP
+
+// ------------------------------------------------------------------------------ grouped-row format
+// One thread per group of G consecutive rows: a G-way merge of the rows' sorted column
+// lists.  Count pass: distinct columns; fill pass: one record per distinct column with the
+// G rows' A and B values (zero where a row lacks the column) and the column index.
+__global__ void grp_count_kernel(int64_t n, int G, const int64_t *__restrict__ rowptr,
+                                 const int32_t *__restrict__ col, int *__restrict__ cnt) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = g * G;
+  if (i0 >= n) return;
+  int64_t pos[4], end[4];
+  const int rows = (int)(n - i0 < G ? n - i0 : G);
+  for (int j = 0; j < rows; ++j) { pos[j] = rowptr[i0 + j]; end[j] = rowptr[i0 + j + 1]; }
+  int c = 0;
+  for (;;) {
+    int32_t m = INT32_MAX;
+    bool any = false;
+    for (int j = 0; j < rows; ++j)
+      if (pos[j] < end[j]) { any = true; m = min(m, col[pos[j]]); }
+    if (!any) break;
+    ++c;
+    for (int j = 0; j < rows; ++j)
+      if (pos[j] < end[j] && col[pos[j]] == m) ++pos[j];
+  }
+  cnt[g] = c;
+}
+
+template <typename R, int G>
+__global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                const double *__restrict__ valA, const double *__restrict__ valB,
+                                const int64_t *__restrict__ gptr, unsigned char *__restrict__ rec) {
+  constexpr int RS = grec_bytes<G>();
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = g * G;
+  if (i0 >= n) return;
+  int64_t pos[G], end[G];
+  const int rows = (int)(n - i0 < G ? n - i0 : G);
+  for (int j = 0; j < G; ++j) {
+    pos[j] = j < rows ? rowptr[i0 + j] : 0;
+    end[j] = j < rows ? rowptr[i0 + j + 1] : 0;
+  }
+  int64_t e = gptr[g];
+  for (;;) {
+    int32_t m = INT32_MAX;
+    bool any = false;
+    for (int j = 0; j < G; ++j)
+      if (pos[j] < end[j]) { any = true; m = min(m, col[pos[j]]); }
+    if (!any) break;
+    unsigned char *rp = rec + (size_t)e * RS;
+    for (int j = 0; j < G; ++j) {
+      double av = 0.0, bv = 0.0;
+      if (pos[j] < end[j] && col[pos[j]] == m) {
+        av = valA[pos[j]];
+        bv = valB[pos[j]];
+        ++pos[j];
+      }
+      if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float2 *>(rp)[j] = make_float2((float)av, (float)av);
+        reinterpret_cast<float2 *>(rp)[G + j] = make_float2((float)bv, (float)bv);
+      } else {
+        reinterpret_cast<double *>(rp)[j] = av;
+        reinterpret_cast<double *>(rp)[G + j] = bv;
+      }
+    }
+    *reinterpret_cast<int *>(rp + 16 * G) = m;
+    ++e;
+  }
+}
+
+void grp_count(int64_t n, int G, const int64_t *rowptr, const int32_t *col, int *cnt, cudaStream_t st) {
+  const int64_t ng = (n + G - 1) / G;
+  grp_count_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(n, G, rowptr, col, cnt);
+}
+template <typename R>
+void grp_fill(int64_t n, int G, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+              const int64_t *gptr, unsigned char *rec, cudaStream_t st) {
+  const int64_t ng = (n + G - 1) / G;
+  const unsigned blocks = (unsigned)((ng + 255) / 256);
+  switch (G) {
+    case 2: grp_fill_kernel<R, 2><<<blocks, 256, 0, st>>>(n, rowptr, col, valA, valB, gptr, rec); break;
+    case 3: grp_fill_kernel<R, 3><<<blocks, 256, 0, st>>>(n, rowptr, col, valA, valB, gptr, rec); break;
+    case 4: grp_fill_kernel<R, 4><<<blocks, 256, 0, st>>>(n, rowptr, col, valA, valB, gptr, rec); break;
+    default: grp_fill_kernel<R, 1><<<blocks, 256, 0, st>>>(n, rowptr, col, valA, valB, gptr, rec); break;
+  }
+}
+template void grp_fill<float>(int64_t, int, const int64_t *, const int32_t *, const double *, const double *,
+                              const int64_t *, unsigned char *, cudaStream_t);
+template void grp_fill<double>(int64_t, int, const int64_t *, const int32_t *, const double *, const double *,
+                               const int64_t *, unsigned char *, cudaStream_t);
 
 // ------------------------------------------------------------------------------ prepare
 __global__ void cocg_prepare_kernel(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,
@@ -781,10 +1087,11 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
   }
 #undef UPD
 }
-template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
-                                    cudaStream_t st) {
+template <typename R, int G>
+static void cocg_dual_g(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm, cudaStream_t st) {
   const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
-#define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
+  const int smem = G == 1 ? 0 : grp_smem_bytes<G>();
+#define DUAL(F, M) cocg_dual_kernel<R, F, M, G><<<blocks, kThreads, smem, st>>>(a, s0, ns, u0, nu)
   if (first) DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
   else {
     switch (fm) {
@@ -797,9 +1104,61 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
   }
 #undef DUAL
 }
+template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
+                                    cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    switch (a.G) {
+      case 2: cocg_dual_g<R, 2>(a, s0, ns, u0, nu, first, fm, st); return;
+      case 3: cocg_dual_g<R, 3>(a, s0, ns, u0, nu, first, fm, st); return;
+      case 4: cocg_dual_g<R, 4>(a, s0, ns, u0, nu, first, fm, st); return;
+      default: break;
+    }
+  }
+  cocg_dual_g<R, 1>(a, s0, ns, u0, nu, first, fm, st);
+}
+template <typename R, int G> static void cocg_spmm_grp(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+  if (fresh) cocg_spmm_grp_kernel<R, G, true><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+  else cocg_spmm_grp_kernel<R, G, false><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+}
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+  switch (a.G) {
+    case 2: cocg_spmm_grp<R, 2>(a, st, fresh); return;
+    case 3: cocg_spmm_grp<R, 3>(a, st, fresh); return;
+    case 4: cocg_spmm_grp<R, 4>(a, st, fresh); return;
+    default: break;
+  }
   if (fresh) cocg_spmm_kernel<R, true><<<grid_of(a), kThreads, 0, st>>>(a);
   else cocg_spmm_kernel<R, false><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+
+// Dynamic shared memory above the default 48 KB for every grouped kernel instance
+// (called once per process, before any launch or stream capture).
+template <typename R, int G> static void grp_attrs() {
+  const int sm = grp_smem_bytes<G>();
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (sizeof(R) == 4) {
+    cudaFuncSetAttribute(cocg_dual_kernel<R, true, kFinalNone, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalNone, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalU, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalStoreD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         sm);
+    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalAddD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalUFromD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         sm);
+  }
+}
+void cocg_kernel_attrs() {
+  static bool done = false;
+  if (done) return;
+  grp_attrs<float, 2>();
+  grp_attrs<float, 3>();
+  grp_attrs<float, 4>();
+  grp_attrs<double, 2>();
+  grp_attrs<double, 3>();
+  grp_attrs<double, 4>();
+  cudaGetLastError();
+  done = true;
 }
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st) {
   cocg_residual_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);

@@ -65,7 +65,30 @@ struct CocgArgs {
   const double2 *sig64;
   double *r00;
   int it_cap;  // > 0: a column stops after this many updates (per-problem It_max in a batch)
+  // Grouped-row SpMM (G > 1): rows [G g, G g + G) share one sorted union column list.  Record
+  // e of group g (gptr[g] <= e < gptr[g + 1]) is grec_bytes<G>() bytes: the G rows' A values,
+  // then their B values (FP64: one double each; FP32: each value twice, a float2 pair, the
+  // operand of a packed FP32 FMA), then the column (int32); zero where a row has no entry.
+  // The records of a group reach shared memory by 1-D bulk copies (TMA engine).
+  int G;                     // rows per group; 1 = plain CSR
+  int64_t ngroups;
+  const int64_t *gptr;       // [ngroups + 1]
+  const unsigned char *grec; // records, 16-byte aligned
+  int *err;                  // set to 1 when a bounded wait gives up (SLRF_ETIMEOUT)
+  // Jacobi preconditioner D = diag(A): the value arrays above are those of
+  // D^-1/2 A D^-1/2 and D^-1/2 B D^-1/2, g is D^-1/2 g, and dsc[i] = D_ii^-1/2 turns the
+  // scaled solutions back (y = D^-1/2 z) in the pole sum; null: no preconditioner
+  const double *dsc;
 };
+
+// Record size of the grouped-row SpMM: 2 G values of 8 bytes and the column, rounded up to 16.
+template <int G> __host__ __device__ constexpr int grec_bytes() { return (16 * G + 4 + 15) / 16 * 16; }
+#ifndef SLRF_GRP_CHUNK
+#define SLRF_GRP_CHUNK 32
+#endif
+constexpr int kGrpChunk = SLRF_GRP_CHUNK;  // records per staged chunk (one bulk copy)
+// Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.
+template <int G> __host__ __device__ constexpr int grp_smem_bytes() { return kWarps * 2 * kGrpChunk * grec_bytes<G>(); }
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.
 enum FinalMode { kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, kFinalUFromD = 4 };
@@ -105,6 +128,17 @@ template <typename R> void cocg_spmm_batched_launch(const CocgArgs<R> *args, con
                                                     bool fresh, cudaStream_t st);
 template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
                                                         cudaStream_t st);
+
+// Raise the dynamic shared-memory limit of the grouped SpMM kernels (once per process;
+// call before the first launch and outside stream capture).
+void cocg_kernel_attrs();
+
+// Grouped-row format: cnt[g] = number of distinct columns of rows [G g, G g + G) (grp_count),
+// then the records of every group at the offsets gptr (grp_fill, R = float or double).
+void grp_count(int64_t n, int G, const int64_t *rowptr, const int32_t *col, int *cnt, cudaStream_t st);
+template <typename R>
+void grp_fill(int64_t n, int G, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+              const int64_t *gptr, unsigned char *rec, cudaStream_t st);
 
 // prepare per-w factors: warm start c = 1/(sigma_j - theta_c), else 1; coefV = Phi(theta_c)
 void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2 *wt,

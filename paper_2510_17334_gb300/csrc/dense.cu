@@ -120,7 +120,144 @@ __global__ void __launch_bounds__(256) spmm_b32_kernel(int64_t n, const int64_t 
   }
 }
 
+// YA = A X and YB = B X with FP32 products and sums (FP64 in and out): the real sweep that
+// starts the complex-FP32 solves (q0 = c (A g - sigma B g) only enters FP32 arithmetic).
+template <int U>
+__global__ void __launch_bounds__(256) spmm_ab32_kernel(int64_t n, const int64_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ col,
+                                                        const double *__restrict__ valA,
+                                                        const double *__restrict__ valB,
+                                                        const double *__restrict__ X, int ldx, int k,
+                                                        double *__restrict__ YA, double *__restrict__ YB, int ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * kSpmmRows + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int c0 = blockIdx.y * (32 * U) + lane;
+  const char *const xl = reinterpret_cast<const char *>(X + c0);
+  const unsigned row_bytes = (unsigned)ldx * (unsigned)sizeof(double);
+  float sa[U], sb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) sa[u] = sb[u] = 0.f;
+  const int64_t rs = rowptr[i], re = rowptr[i + 1];
+  for (int64_t e0 = rs; e0 < re; e0 += 32) {
+    const int cnt = (int)(re - e0 < 32 ? re - e0 : 32);
+    int cl = 0;
+    float al = 0.f, bl = 0.f;
+    if (lane < cnt) {
+      cl = col[e0 + lane];
+      al = (float)valA[e0 + lane];
+      bl = (float)valB[e0 + lane];
+    }
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) {
+      const int c = __shfl_sync(0xffffffffu, cl, t);
+      const float a = __shfl_sync(0xffffffffu, al, t);
+      const float b = __shfl_sync(0xffffffffu, bl, t);
+      const double *xr = reinterpret_cast<const double *>(xl + (unsigned long long)(unsigned)c * row_bytes);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c0 + 32 * u < k) {
+          const float x = (float)xr[32 * u];
+          sa[u] = fmaf(a, x, sa[u]);
+          sb[u] = fmaf(b, x, sb[u]);
+        }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int cc = c0 + 32 * u;
+    if (cc < k) {
+      YA[(size_t)i * ldy + cc] = (double)sa[u];
+      YB[(size_t)i * ldy + cc] = (double)sb[u];
+    }
+  }
+}
+
 static int spmm_lanes(int k) { return std::min(8, (k + 31) / 32); }
+
+void spmm_ab32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return;
+  const int U = spmm_lanes(k);
+  dim3 grid((unsigned)((n + kSpmmRows - 1) / kSpmmRows), (unsigned)((k + 32 * U - 1) / (32 * U)));
+#define SPMM_AB32(UU) spmm_ab32_kernel<UU><<<grid, 256, 0, st>>>(n, rowptr, col, valA, valB, X, ldx, k, YA, YB, ldy)
+  switch (U) {
+    case 1: SPMM_AB32(1); break;
+    case 2: SPMM_AB32(2); break;
+    case 3: SPMM_AB32(3); break;
+    case 4: SPMM_AB32(4); break;
+    case 5: SPMM_AB32(5); break;
+    case 6: SPMM_AB32(6); break;
+    case 7: SPMM_AB32(7); break;
+    default: SPMM_AB32(8); break;
+  }
+#undef SPMM_AB32
+}
+
+// Jacobi preconditioner: dsc[i] = A_ii^-1/2 (flag = 1 when a diagonal entry is missing or
+// not positive), then the scaled values A_ij dsc_i dsc_j and B_ij dsc_i dsc_j.
+__global__ void jacobi_diag_kernel(int64_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                   const double *__restrict__ valA, double *__restrict__ dsc, int *flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+    if (col[e] == i) d = valA[e];
+  if (d > 0.0 && isfinite(d)) {
+    dsc[i] = 1.0 / sqrt(d);
+  } else {
+    dsc[i] = 1.0;
+    atomicExch(flag, 1);
+  }
+}
+__global__ void jacobi_values_kernel(int64_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                     const double *__restrict__ valA, const double *__restrict__ valB,
+                                     const double *__restrict__ dsc, double *__restrict__ valAs,
+                                     double *__restrict__ valBs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const double di = dsc[i];
+  for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+    const double s = di * dsc[col[e]];
+    valAs[e] = valA[e] * s;
+    valBs[e] = valB[e] * s;
+  }
+}
+void jacobi_scaling(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+                    double *dsc, double *valAs, double *valBs, int *flag, cudaStream_t st) {
+  jacobi_diag_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, rowptr, col, valA, dsc, flag);
+  jacobi_values_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, rowptr, col, valA, valB, dsc, valAs, valBs);
+}
+// CSR sanity: rowptr[0] = 0, non-decreasing, rowptr[n] = nnz, 0 <= col < n.  *flag = 1 on failure.
+__global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+    const int64_t r = rowptr[i];
+    if (r < 0 || r > nnz || (i == 0 && r != 0) || (i == n && r != nnz) || (i > 0 && rowptr[i - 1] > r))
+      atomicExch(flag, 1);
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = col[e];
+    if (c < 0 || (int64_t)c >= n) atomicExch(flag, 1);
+  }
+}
+void validate_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag, int blocks,
+                  cudaStream_t st) {
+  validate_csr_kernel<<<blocks, 256, 0, st>>>(n, nnz, rowptr, col, flag);
+}
+
+__global__ void row_scale_kernel(int64_t n, int k, const double *__restrict__ s, double *X, int ldx) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t / k;
+  X[i * ldx + t % k] *= s[i];
+}
+void row_scale(int64_t n, int k, const double *s, double *X, int ldx, cudaStream_t st) {
+  const int64_t tot = n * k;
+  if (tot <= 0) return;
+  row_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, s, X, ldx);
+}
 
 void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
                const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st,

@@ -14,6 +14,20 @@ void spmm_real(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
 void spmm_b32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valB, const double *X, int ldx,
               int k, double *YB, int ldy, cudaStream_t st);
 
+// YA = A X and YB = B X in FP32 arithmetic (FP64 storage): the start of the FP32 solves.
+void spmm_ab32(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+               const double *X, int ldx, int k, double *YA, double *YB, int ldy, cudaStream_t st);
+// Jacobi preconditioner D = diag(A): dsc = D^-1/2 (*flag = 1 if a diagonal entry is missing or
+// not positive) and the values of D^-1/2 A D^-1/2, D^-1/2 B D^-1/2 on the same pattern.
+void jacobi_scaling(int64_t n, const int64_t *rowptr, const int32_t *col, const double *valA, const double *valB,
+                    double *dsc, double *valAs, double *valBs, int *flag, cudaStream_t st);
+// CSR sanity check before any kernel gathers through a caller's pattern: rowptr[0] = 0,
+// non-decreasing, rowptr[n] = nnz, 0 <= col < n; sets *flag = 1 otherwise (grid of blocks x 256).
+void validate_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag, int blocks,
+                  cudaStream_t st);
+// X[i][:] *= s[i] (row-major n x k, leading dimension ldx).
+void row_scale(int64_t n, int k, const double *s, double *X, int ldx, cudaStream_t st);
+
 // R = AV - theta .* BV (column-wise theta), row-major n x k.
 void shifted_residual(int64_t n, int k, const double *AV, const double *BV, int ld, const double *theta,
                       double *R, int ldr, cudaStream_t st);

@@ -54,7 +54,16 @@ struct slrf_ctx {
   int64_t *rowptr = nullptr;
   int32_t *col = nullptr;
   double *valA = nullptr, *valB = nullptr;
-  float *valA32 = nullptr, *valB32 = nullptr;
+  float *valA32 = nullptr, *valB32 = nullptr;  // FP32 copies of the values the COCG uses
+  // Jacobi preconditioner (opts.precond): D^-1/2 per row and the scaled FP64 values the
+  // COCG and its starting sweep use (valA / valB stay the pencil's own values)
+  double *dsc = nullptr, *valAs = nullptr, *valBs = nullptr;
+  // grouped-row format of the COCG SpMM (grp > 1 rows per group)
+  int grp = 1;
+  int64_t ngroups = 0;
+  int64_t *gptr = nullptr;
+  unsigned char *grec = nullptr;
+  int sm_count = 152;  // multiprocessors of the device (grid sizing)
   // pole table
   double2 *sig = nullptr, *wt = nullptr;
   float2 *sig32 = nullptr;
@@ -130,6 +139,13 @@ template <typename T> static int dalloc(slrf_ctx *ctx, T **p, size_t count) {
   return SLRF_OK;
 }
 
+static void dfree(slrf_ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  cudaFree(p);
+}
+
 static int pow2_at_least(int m) {
   int p = 1;
   while (p < m) p <<= 1;
@@ -143,19 +159,10 @@ static int kpad_of(int k, int mp, int vec) {
   return W / mp;
 }
 
-// CSR sanity: rowptr[0] = 0, non-decreasing, rowptr[n] = nnz, 0 <= col < n.  flag[0] = 1 on failure.
-__global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
-    const int64_t r = rowptr[i];
-    if (r < 0 || r > nnz || (i == 0 && r != 0) || (i == n && r != nnz) || (i > 0 && rowptr[i - 1] > r))
-      atomicExch(flag, 1);
-  }
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-    const int32_t c = col[e];
-    if (c < 0 || (int64_t)c >= n) atomicExch(flag, 1);
-  }
-}
+// FP64 values of the shifted systems the COCG solves (scaled when preconditioned).
+static const double *cocg_valA(const slrf_ctx *c) { return c->dsc ? c->valAs : c->valA; }
+static const double *cocg_valB(const slrf_ctx *c) { return c->dsc ? c->valBs : c->valB; }
+
 
 __global__ void to_float_kernel(int64_t count, const double *a, float *b) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -214,10 +221,94 @@ __global__ void final_gather_kernel(int64_t n, int nconv, int cnt, const int *ra
   }
 }
 
+// ----------------------------------------------------------------------------- grouped rows
+// The COCG SpMM's grouped-row format (CocgArgs): rows [G g, G g + G) share one union
+// column list.  group_counts returns the union sizes for a G; build_groups writes the
+// offsets and the records of the working precision; choose_group picks G.
+static int group_counts(slrf_ctx *ctx, int G, std::vector<int> &cnt) {
+  const int64_t ng = (ctx->n + G - 1) / G;
+  int *d = nullptr;
+  if (cudaMalloc(&d, (size_t)ng * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return SLRF_ENOMEM;
+  }
+  grp_count(ctx->n, G, ctx->rowptr, ctx->col, d, ctx->st);
+  cnt.resize((size_t)ng);
+  cudaError_t e = cudaMemcpyAsync(cnt.data(), d, (size_t)ng * sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(d);
+  return e == cudaSuccess ? SLRF_OK : SLRF_ECUDA;
+}
+static int grec_size(int G) { return (16 * G + 4 + 15) / 16 * 16; }
+static void drop_groups(slrf_ctx *ctx) {
+  dfree(ctx, ctx->gptr);
+  dfree(ctx, ctx->grec);
+  ctx->gptr = nullptr;
+  ctx->grec = nullptr;
+  ctx->grp = 1;
+  ctx->ngroups = 0;
+}
+static int build_groups(slrf_ctx *ctx, int G) {
+  drop_groups(ctx);
+  if (G <= 1) return SLRF_OK;
+  std::vector<int> cnt;
+  int rc = group_counts(ctx, G, cnt);
+  if (rc != SLRF_OK) return rc;
+  const int64_t ng = (int64_t)cnt.size();
+  std::vector<int64_t> off((size_t)ng + 1, 0);
+  for (int64_t g = 0; g < ng; ++g) off[g + 1] = off[g] + cnt[g];
+  if ((rc = dalloc(ctx, &ctx->gptr, (size_t)ng + 1)) != SLRF_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->grec, (size_t)off[ng] * grec_size(G) + 16)) != SLRF_OK) return rc;
+  if (cudaMemcpyAsync(ctx->gptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st) !=
+      cudaSuccess)
+    return SLRF_ECUDA;
+  if (ctx->mixed)
+    grp_fill<float>(ctx->n, G, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->gptr, ctx->grec, ctx->st);
+  else
+    grp_fill<double>(ctx->n, G, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->gptr, ctx->grec, ctx->st);
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
+  ctx->grp = G;
+  ctx->ngroups = ng;
+  return SLRF_OK;
+}
+// Candidate G from the pattern.  FP64: the SpMM is bound by the FP64 pipe, so only groups
+// that add no zero products qualify (union x rows == entries), the largest such G.  FP32:
+// a cost model per row of one warp tile (64 complex entries): a gathered row costs its
+// L1 traffic (512 B, ~4 cycles) or the packed FMAs it feeds (8 G per lane, 2 G cycles),
+// whichever is larger; plain CSR pays ~4.6 cycles per entry (gather plus shuffles).
+static int choose_group(slrf_ctx *ctx, int &G) {
+  G = 1;
+  double best = (double)ctx->nnz / ctx->n * 4.6;
+  for (int g = (ctx->mixed ? 2 : 4); ctx->mixed ? g <= 4 : g >= 2; g += ctx->mixed ? 1 : -1) {
+    std::vector<int> cnt;
+    int rc = group_counts(ctx, g, cnt);
+    if (rc != SLRF_OK) return rc;
+    double recs = 0, slots = 0;
+    for (size_t i = 0; i < cnt.size(); ++i) {
+      recs += cnt[i];
+      slots += (double)cnt[i] * (double)std::min<int64_t>(g, ctx->n - (int64_t)i * g);
+    }
+    if (!ctx->mixed) {
+      if (slots <= (double)ctx->nnz) { G = g; return SLRF_OK; }
+      continue;
+    }
+    const double cost = recs / ctx->n * std::max(4.0, 2.0 * g);
+    if (cost < best) { best = cost; G = g; }
+  }
+  return SLRF_OK;
+}
+static int setup_groups(slrf_ctx *ctx) {
+  int G = ctx->o.group;
+  if (G == 0) {
+    int rc = choose_group(ctx, G);
+    if (rc != SLRF_OK) return rc;
+  }
+  return build_groups(ctx, G);
+}
+
 // ----------------------------------------------------------------------------- filter
 // U = sum_j 2 Re(w_j Y_j), (A - sigma_j B) Y_j = B X, in correction form (see cocg.cu).
 // AXp/BXp: A X and B X if already known (warm start), else computed here.
-constexpr int64_t kRowBlocks = 152 * 4;
 
 // Optional per-kernel timing of one filter apply (measurement hook, direct launches).
 struct FilterTiming {
@@ -231,22 +322,30 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   const int vec = cocg_vec<R>();
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
-  // Row blocks per tile: about as many as the GPU holds resident (152 SMs x 4 blocks), so
+  // Row blocks per tile: about as many as the GPU holds resident (SMs x 4 blocks), so
   // that the blocks in flight at any time all belong to one or two tiles (the tile index
   // varies slowest) and the gathered rows of those tiles stay in L2.  An autotuned row
   // count (slrf_opts.autotune) replaces the default.
-  int64_t rpb = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
+  const int64_t rblocks = (int64_t)ctx->sm_count * 4;
+  int64_t rpb = std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
   if (ctx->rpb_tuned > 0) rpb = std::max<int64_t>(rpb, ctx->rpb_tuned);
+  rpb = (rpb + ctx->grp - 1) / ctx->grp * ctx->grp;  // whole groups per row block
   const int nrb = (int)((ctx->n + rpb - 1) / rpb);
   CocgArgs<R> a{};
   a.n = ctx->n;
   a.rowptr = ctx->rowptr;
   a.col = ctx->col;
   if constexpr (sizeof(R) == 8) {
-    a.valA = ctx->valA; a.valB = ctx->valB; a.sig = ctx->sig;
+    a.valA = cocg_valA(ctx); a.valB = cocg_valB(ctx); a.sig = ctx->sig;
   } else {
     a.valA = ctx->valA32; a.valB = ctx->valB32; a.sig = ctx->sig32;
   }
+  a.G = ctx->grp;
+  a.ngroups = ctx->ngroups;
+  a.gptr = ctx->gptr;
+  a.grec = ctx->grec;
+  a.err = ctx->iflags + 15;
+  a.dsc = ctx->dsc;
   a.W = W; a.k = k; a.m = ctx->m; a.mp = ctx->mp;
   a.rows_per_block = (int)rpb; a.nrb = nrb;
   a.d = (cx_t<R> *)ctx->cd; a.r = (cx_t<R> *)ctx->cr; a.p = (cx_t<R> *)ctx->cp; a.q = (cx_t<R> *)ctx->cq;
@@ -260,8 +359,8 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   nref = (sizeof(R) == 4 && ctx->D64 != nullptr) ? std::max(1, ctx->o.refine_max) : 1;
   if (nref > 1) {
     a.D64 = ctx->D64;
-    a.valA64 = ctx->valA;
-    a.valB64 = ctx->valB;
+    a.valA64 = cocg_valA(ctx);
+    a.valB64 = cocg_valB(ctx);
     a.sig64 = ctx->sig;
     a.r00 = ctx->r00;
   }
@@ -386,7 +485,16 @@ static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
     shifted_residual(ctx->n, k, AX, BX, ldab, theta, ctx->G, L, st);
     ctx->launches += 1;
   }
-  spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->G, L, k, ctx->AG, ctx->BG, L, st);
+  // preconditioned: the solves start from D^-1/2 g and the scaled matrices
+  if (ctx->dsc != nullptr) {
+    row_scale(ctx->n, k, ctx->dsc, ctx->G, L, st);
+    ctx->launches += 1;
+  }
+  // A g and B g only start the COCG recurrences (q0); in the mixed path those run in FP32
+  if (ctx->mixed)
+    spmm_ab32(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
+  else
+    spmm_real(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
   ctx->launches += 1;
   CKL();
   return SLRF_OK;
@@ -400,8 +508,9 @@ static int filter_impl(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
   return run_cocg<double>(ctx, X, ldx, k, theta, U, ldu, capture_ok, tm);
 }
 
-// Autotuner: time one fused SpMM launch for each candidate rows-per-block on a Gaussian
-// block of the full width (after the usual initialisation) and keep the fastest.
+// Autotuner: time the fused SpMM (best of three launches) on a Gaussian block of the full
+// width (after the usual initialisation) for each group height of the grouped-row format
+// (when opts.group = 0), then for each candidate rows-per-block, and keep the fastest.
 template <typename R>
 static int autotune_rows(slrf_ctx *ctx) {
   const cudaStream_t st = ctx->st;
@@ -409,35 +518,62 @@ static int autotune_rows(slrf_ctx *ctx) {
   gaussian_block(ctx->n, L, ctx->o.seed + 7, ctx->V, L, st);
   int rc = filter_prep(ctx, ctx->V, L, L, nullptr, nullptr, nullptr);
   if (rc != SLRF_OK) return rc;
-  const int64_t base = std::max<int64_t>(16, (ctx->n + kRowBlocks - 1) / kRowBlocks);
-  const int64_t cand[] = {base, 32, 64, 128, 256};
+  const int64_t rblocks = (int64_t)ctx->sm_count * 4;
+  const int64_t base = std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int64_t best_r = 0;
-  for (int64_t c : cand) {
-    if (c < base || c > ctx->n) continue;
-    ctx->rpb_tuned = c;
+  // best of three SpMM launches with the current group height and rows per block
+  auto time_spmm = [&](float &t) -> int {
     int nref = 1;
     CocgArgs<R> a = build_cocg_args<R>(ctx, ctx->V, L, L, ctx->U, L, nref);
     cocg_prepare(a.W, L, ctx->m, ctx->mp, ctx->sig, ctx->wt, nullptr, ctx->cfac, ctx->coefV, ctx->ws, st);
     if (sizeof(R) == 4) col_scale(ctx->n, L, ctx->G, L, ctx->gmax, ctx->gscale, st);
     cocg_init<R>(a, st);
-    float t = 1e30f;
+    t = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, st);
       cocg_spmm<R>(a, st);
       cudaEventRecord(e1, st);
-      CK(cudaEventSynchronize(e1));
+      if (cudaEventSynchronize(e1) != cudaSuccess) return SLRF_ECUDA;
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       t = std::min(t, ms);
     }
+    return SLRF_OK;
+  };
+  float best = 1e30f, t = 0;
+  if (ctx->o.group == 0) {
+    // group height: plain CSR and every grouped format the precision admits (FP64: the
+    // no-fill height the pattern model found, if any; FP32: 2, 3 and 4)
+    const int g_model = ctx->grp;
+    int best_g = 1;
+    for (int g = 1; g <= 4; ++g) {
+      if (g > 1 && !ctx->mixed && g != g_model) continue;
+      if ((rc = build_groups(ctx, g)) != SLRF_OK) break;
+      ctx->rpb_tuned = 0;
+      if ((rc = time_spmm(t)) != SLRF_OK) break;
+      if (t < best) { best = t; best_g = g; }
+    }
+    if (rc == SLRF_OK) rc = build_groups(ctx, best_g);
+    if (rc != SLRF_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+  }
+  const int64_t cand[] = {base, 32, 64, 128, 256};
+  best = 1e30f;
+  int64_t best_r = 0;
+  for (int64_t c : cand) {
+    if (c < base || c > ctx->n) continue;
+    ctx->rpb_tuned = c;
+    if ((rc = time_spmm(t)) != SLRF_OK) break;
     if (t < best) { best = t; best_r = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc != SLRF_OK) return rc;
   ctx->rpb_tuned = best_r;
   CKL();
   return SLRF_OK;
@@ -773,7 +909,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   if (opts) o = *opts;
   else slrf_opts_default(&o);
   if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1 || o.dense < 0 || o.dense > 1 ||
-      o.it_adapt < 0 || o.it_adapt > 1)
+      o.it_adapt < 0 || o.it_adapt > 1 || o.precond < 0 || o.precond > 1 || o.group < 0 || o.group > 4)
     return SLRF_EINVAL;
   if (block_L > 510) return SLRF_EINVAL;  // the projected eigensolver holds two rows of <= 512 in shared memory
   if (!(o.tol_inner >= 0) || !(o.tol_eig > 0)) return SLRF_EINVAL;
@@ -786,6 +922,10 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   };
   ctx->ust = (cudaStream_t)stream;
   cudaGetDevice(&ctx->dev);
+  if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->dev) != cudaSuccess ||
+      ctx->sm_count < 1)
+    return fail(SLRF_ECUDA);
+  cocg_kernel_attrs();
   if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
@@ -810,8 +950,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   const size_t csz = ctx->mixed ? 8 : 16;
   const size_t state = 4 * (size_t)n * ctx->Wmax * csz;
   const size_t ntiles_max = ctx->Wmax / (32 * ctx->vec);
-  // run_cocg uses at most kRowBlocks row blocks for any k <= L
-  const size_t partial = (size_t)kRowBlocks * ctx->Wmax * kNQ;
+  // run_cocg uses at most 4 row blocks per SM for any k <= L
+  const size_t partial = (size_t)ctx->sm_count * 4 * ctx->Wmax * kNQ;
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
   const size_t refine = (ctx->mixed && o.refine_max > 1) ? 16 * (size_t)n * ctx->Wmax : 0;
@@ -837,7 +977,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
     int bad = 0;
     cudaMemsetAsync(ctx->valA + ctx->nnz, 0, sizeof(double), ctx->st);
     int *dflag = reinterpret_cast<int *>(ctx->valA + ctx->nnz);
-    validate_csr_kernel<<<152 * 4, 256, 0, ctx->st>>>(n, ctx->nnz, ctx->rowptr, ctx->col, dflag);
+    validate_csr(n, ctx->nnz, ctx->rowptr, ctx->col, dflag, ctx->sm_count * 4, ctx->st);
     if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess)
       return fail(SLRF_ECUDA);
@@ -846,13 +986,28 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   AL(ctx->sig, 32);
   AL(ctx->wt, 32);
   AL(ctx->sig32, 32);
+  if (o.precond) {
+    // Jacobi preconditioner: D^-1/2 and the scaled values of both matrices
+    AL(ctx->dsc, (size_t)n);
+    AL(ctx->valAs, (size_t)ctx->nnz + 4);
+    AL(ctx->valBs, (size_t)ctx->nnz + 4);
+    int bad = 0;
+    int *dflag = reinterpret_cast<int *>(ctx->valAs + ctx->nnz);
+    cudaMemsetAsync(dflag, 0, sizeof(int), ctx->st);
+    jacobi_scaling(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->dsc, ctx->valAs, ctx->valBs, dflag, ctx->st);
+    if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess)
+      return fail(SLRF_ECUDA);
+    if (bad) return fail(SLRF_EINVAL);
+  }
   if (ctx->mixed) {
     AL(ctx->valA32, (size_t)ctx->nnz + 4);
     AL(ctx->valB32, (size_t)ctx->nnz + 4);
     const unsigned gb = (unsigned)((ctx->nnz + 255) / 256);
-    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, ctx->valA, ctx->valA32);
-    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, ctx->valB, ctx->valB32);
+    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, cocg_valA(ctx), ctx->valA32);
+    to_float_kernel<<<gb, 256, 0, ctx->st>>>(ctx->nnz, cocg_valB(ctx), ctx->valB32);
   }
+  if ((rc = setup_groups(ctx)) != SLRF_OK) return fail(rc);
   AL(ctx->iflags, 16);
   if (cudaMallocHost(&ctx->h_iflags, 16 * sizeof(int)) != cudaSuccess) return fail(SLRF_ENOMEM);
   cudaMemsetAsync(ctx->iflags, 0, 16 * sizeof(int), ctx->st);
@@ -1115,7 +1270,7 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
       ms_d += b;
     }
     const int *hf = ctx->h_iflags;
-    if (hf[9] != 0 || hf[13] != 0) { status = SLRF_ETIMEOUT; break; }
+    if (hf[9] != 0 || hf[13] != 0 || hf[15] != 0) { status = SLRF_ETIMEOUT; break; }
     if (hf[4] != 0) { status = SLRF_ECHOL; break; }
     nconv = hf[0];
     k = hf[1];
@@ -1230,8 +1385,13 @@ int slrf_setup_batched(slrf_batch **out, int P, const slrf_csr_pair *pencils, co
   b->ust = (cudaStream_t)stream;
   b->c.assign(P, nullptr);
   b->ev_p.assign(P, nullptr);
+  // the persistent batched launches gather through the plain CSR pattern of each problem
+  slrf_opts ob;
+  if (opts) ob = *opts;
+  else slrf_opts_default(&ob);
+  ob.group = 1;
   for (int p = 0; p < P; ++p) {
-    const int rc = slrf_setup(&b->c[p], &pencils[p], gammas[p], blocks[p], opts, stream);
+    const int rc = slrf_setup(&b->c[p], &pencils[p], gammas[p], blocks[p], &ob, stream);
     if (rc != SLRF_OK) {
       batch_free(b);
       return rc;

@@ -52,7 +52,7 @@ class Opts(ct.Structure):
                 ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
                 ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
                 ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int),
-                ("dense", ct.c_int), ("it_adapt", ct.c_int)]
+                ("dense", ct.c_int), ("it_adapt", ct.c_int), ("precond", ct.c_int), ("group", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -346,13 +346,35 @@ def tsgemm(X: torch.Tensor, S: torch.Tensor, Z: torch.Tensor | None = None, alph
 
 def filter_apply_static(rowptr, col, valA, valB, gamma, opts, X, theta=None, U=None, stream=None):
     """slrf_filter_apply_static: the FP64 filter apply without a context or any device
-    allocation inside the library (device tensors in, U out; the caller's stream)."""
+    allocation inside the library (device tensors in, U out; the stream of X's device
+    unless one is given).  The layouts the C side assumes are checked here: rowptr int64
+    (n + 1), col int32 (nnz), valA / valB float64 (nnz), X and U float64 n x k contiguous,
+    theta float64 (k), all on one CUDA device.  Pass a preallocated U to avoid the one
+    allocation this wrapper would otherwise make."""
+    dev = X.device
     n = int(rowptr.numel() - 1)
+    nnz = int(col.numel())
+
+    def need(t, dtype, shape, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == dev and t.dtype == dtype
+                and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"{name}: expected a contiguous {dtype} tensor of shape {shape} on {dev}")
+
+    if not X.is_cuda or X.dim() != 2:
+        raise ValueError("X: expected a 2-D CUDA tensor")
     k = int(X.shape[1])
+    need(rowptr, torch.int64, (n + 1,), "rowptr")
+    need(col, torch.int32, (nnz,), "col")
+    need(valA, torch.float64, (nnz,), "valA")
+    need(valB, torch.float64, (nnz,), "valB")
+    need(X, torch.float64, (n, k), "X")
+    if theta is not None:
+        need(theta, torch.float64, (k,), "theta")
     if U is None:
         U = torch.empty_like(X)
-    pair = CsrPair(n, int(col.numel()), _ptr(rowptr), _ptr(col), _ptr(valA), _ptr(valB))
-    st = stream if stream is not None else torch.cuda.current_stream()
+    need(U, torch.float64, (n, k), "U")
+    pair = CsrPair(n, nnz, _ptr(rowptr), _ptr(col), _ptr(valA), _ptr(valB))
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
     _check(lib().slrf_filter_apply_static(ct.byref(pair), float(gamma), ct.byref(opts), _ptr(X), k, _ptr(theta),
                                           _ptr(U), ct.c_void_p(st.cuda_stream)), "slrf_filter_apply_static")
     return U

@@ -4,7 +4,8 @@ sizes solved in one batch, whose COCG phases run as one persistent launch.
 Checks: every problem's eigenvalues against a dense generalized eigensolver (count
 exact; FP64 <= 1e-10 relative, mixed <= 1e-8), residuals <= 1e-8, and -- since the
 batched kernels run the same per-block arithmetic as the single-problem kernels -- the
-FP64 batch is bitwise equal to solving each problem on its own.
+FP64 batch is bitwise equal to solving each problem on its own with the same plain-CSR
+SpMM (slrf_opts.group = 1, the format the persistent batched launches gather through).
 """
 import numpy as np
 import pytest
@@ -50,7 +51,8 @@ def test_batched_solve(slrf_mod, precision):
         assert np.all(np.abs(ev - lam[:cnt]) <= np.maximum(tol * lam[:cnt], 1e-9 * lam[0])), i
         assert rs.max().item() <= 1e-8
         if precision == 0:
-            ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, g, L, opts)
+            opts1 = slrf_mod.slrf_opts_default(it_max=40, precision=precision, group=1)
+            ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, g, L, opts1)
             _, nf1, ev1, X1, rs1, _ = ctx.solve(torch.from_numpy(V0[i]))
             assert nf1 == nf and np.array_equal(ev1.cpu().numpy(), ev), i
             assert torch.equal(X1, X), i
