@@ -24,19 +24,27 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "eigenpairs/s and shifted column-solves/s at resid≤1e-8; SpMM HBM GB/s vs peak"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz
-# DRAM bytes (read + write) of one cocg_spmm_kernel<double> launch on the 41^3 workload at
-# 160 columns x 8 poles, from the ncu capture summarised in profiles/launches_q1_lap_41_fp64.md
-SPMM64_TRAFFIC_Q1_41 = 5978269696 + 2815613952
+METRIC = "eigenpairs/s and shifted column-solves/s at resid\u22641e-8; SpMM HBM GB/s vs peak"
+# Derived ALU peaks of GB300 (152 SMs at 2.07 GHz): FP64 2 FMA/clock/SM (measured 1.197 TFLOP/s
+# at 1.98 GHz), FP32 128 FMA/clock/SM.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+DEFAULT_WORKLOAD = "elast_64"
+# It_max of the timed solves per workload (swept on GB300; see the design notes): (mixed, FP64)
+DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 20, "bar1d_2000": 200}
+DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 20, "bar1d_2000": 200}
+# Jacobi preconditioner on by default for the elasticity boxes (reading R18)
+DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
 
 
-# Counts of one solve of each workload by Alg. 2 (column-iterations = COCG updates summed
-# over all (pole, column) systems and outer iterations), used to scale the timed oracle
-# sample of the reference arm to a whole solve.
-SOLVE_COUNTS = {"q1_lap_41": {"n_found": 105, "outer": 18, "column_iterations": 145920},
-                "bar1d_2000": {"n_found": 20, "outer": 8, "column_iterations": 358400},
-                "elast_32": {"n_found": 60, "outer": 20, "column_iterations": 448640}}
+def measured_hbm_gbs():
+    """Copy bandwidth of the GB300s (MEASURED_PEAKS.json, driver-written), else the
+    fallback figure of an earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
 
 
 def reduce_over_ranks(found: int, ms: float, world: int, device: str = "cuda"):
@@ -68,15 +76,17 @@ def workload(name: str, it_max: int | None):
         wl.it_max = it_max or 40
         desc = (f"3D Q1 Laplacian + consistent mass, {nodes}^3 nodes (n={wl.n}), Neumann + 1e-3 B, "
                 f"gamma={wl.gamma:.4f} ({wl.n_expected} eigenpairs), block {wl.block}, m=8")
-    elif name in ("elast_32", "elast_48"):
+    elif name in ("elast_32", "elast_48", "elast_64"):
         from slrf_inputs import elastic as se
 
         p = se.pencil(name)
         g, cnt = se.gamma(name)
         spec = se.SPECS[name]
-        wl = si.Workload(name, p, g, spec["block"], 8, spec["seed"], it_max or 40, cnt)
-        desc = (f"3D Q1 elasticity {spec['nodes']} nodes, z=0 clamped (n={p.n}, nnz={p.nnz}), E lognormal(0,0.5), "
-                f"nu=0.3, gamma={g:.4f} ({cnt} eigenpairs), block {spec['block']}, m=8")
+        wl = si.Workload(name, p, g, spec["block"], 8, spec["seed"], it_max or DEFAULT_IT_MAX.get(name, 40), cnt)
+        nx, ny, nz = spec["nodes"]
+        desc = (f"3D Q1 elasticity {nx}x{ny}x{nz} nodes, z=0 clamped (n={p.n:,}, nnz={p.nnz:,}, 3 dof/node), "
+                f"E lognormal(0,0.5) seed {spec['seed']}, nu=0.3, rho=1, gamma={g:.6g} ({cnt} eigenpairs), "
+                f"block {spec['block']}, m=8")
     elif name == "bar1d_2000":
         wl = si.bar1d(2000)
         wl.it_max = it_max or 200
@@ -132,46 +142,147 @@ def clocks_stop(p, f, dev_index: int):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(name: str, it_max: int, n_found: int, col_iters: int, outer: int, budget_s: float = 20.0):
-    """Time the oracle on a bounded sample of the workload and scale it to eigenpairs/s.
+_W = {}  # per-process state of the oracle workers
 
-    Sample: the oracle's filter apply on the first c start-block columns (all m poles,
-    It_max COCG updates) and one Rayleigh-Ritz step on the full block.  The estimate
-    scales the per-column-iteration time by the column-iterations and the RR time by the
-    outer iterations that the GPU solve of the same workload performed."""
+
+def _oracle_worker_init(path):
+    """Process-pool initialiser: one BLAS thread per process, the pencil and the sampled
+    start columns from the shared file (the workers are started with spawn)."""
+    import numpy as np
+    import scipy.sparse as sp
+
+    d = np.load(path)
+    n = int(d["n"])
+    _W["A"] = sp.csr_matrix((d["valA"], d["col"], d["rowptr"]), shape=(n, n))
+    _W["B"] = sp.csr_matrix((d["valB"], d["col"], d["rowptr"]), shape=(n, n))
+    _W["V"] = d["V"]
+    _W["theta"] = d["theta"]
+    _W["gamma"] = float(d["gamma"])
+    _W["m"] = int(d["m"])
+    _W["precond"] = int(d["precond"])
+
+
+def _oracle_worker_filter(task):
+    """The oracle's filter apply (all m poles, `its` COCG updates, warm start) on columns
+    [lo, hi) of the sample; returns the COCG updates it performed."""
+    lo, hi, its = task
+    from oracle import slrf_oracle as orc
+
+    A, B = _W["A"], _W["B"]
+    sig, w = orc.slrf_poles(_W["m"], _W["gamma"])
+    d = A.diagonal() if _W["precond"] else None
+    _, info = orc.filter_apply(A, B, _W["V"][:, lo:hi], _W["theta"][lo:hi], sig, w, its, 1e-10, d)
+    return int(info.iters.sum())
+
+
+def cpu_baseline_sample(name: str, it_max: int, precond: int, n_found: int, col_iters: int, outer: int,
+                        col_solves: int, m: int = 8, budget_s: float = 25.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload, on every host core,
+    scaled to one whole solve with the counts of the GPU solve of the same run.
+
+    Sample: (i) the oracle's warm-started filter apply (Alg. 2; theta spread over (0, gamma])
+    on one start-block column per core, all m poles, a few COCG updates each, the columns in
+    a spawn-started process pool of os.cpu_count() processes with one BLAS thread each ->
+    seconds per column-iteration with every core busy; (ii) one Cholesky-QR2 + Rayleigh-Ritz
+    step of the oracle on a column subset with all cores in BLAS, its sparse part scaled
+    linearly and its dense part quadratically to the solve's mean active block.  Estimate:
+    column-iterations x (i) + outer iterations x (ii)."""
+    import multiprocessing as mp
+    import tempfile
+
     import numpy as np
 
     import slrf_inputs as si
     from oracle import slrf_oracle as orc
 
+    cores = os.cpu_count() or 1
     wl, _ = workload(name, it_max)
     p = wl.pencil
-    A, B = p.A(), p.B()
-    V1 = si.start_block(p.n, wl.block, wl.seed)
-    sig, w = orc.slrf_poles(wl.m, wl.gamma)
-    c = 1
-    t0 = time.perf_counter()
-    _, info = orc.filter_apply(A, B, V1[:, :c], None, sig, w, wl.it_max, 1e-10)
-    t_f = time.perf_counter() - t0
-    # grow the sample while it stays within the budget
-    if t_f < budget_s / 4:
-        c = max(1, min(wl.block, int(c * (budget_s / 2) / max(t_f, 1e-3))))
-        t0 = time.perf_counter()
-        _, info = orc.filter_apply(A, B, V1[:, :c], None, sig, w, wl.it_max, 1e-10)
-        t_f = time.perf_counter() - t0
-    its = int(info.iters.sum())
-    t0 = time.perf_counter()
-    U, _ = orc.cholqr2(V1.copy(), B)
-    orc.rayleigh_ritz(U, A)
-    t_rr = time.perf_counter() - t0
+    k = wl.block
+    V1 = si.start_block(p.n, k, wl.seed)
+    c = min(k, cores)
+    cols = np.ascontiguousarray(V1[:, :c])
+    theta = (np.arange(c) + 0.5) / c * wl.gamma
+    tmp = tempfile.NamedTemporaryFile(suffix=".npz", delete=False)
+    tmp.close()
+    np.savez(tmp.name, n=p.n, rowptr=p.rowptr, col=p.col, valA=p.valA, valB=p.valB, V=cols, theta=theta,
+             gamma=wl.gamma, m=m, precond=precond)
+    env_keep = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in env_keep:
+        os.environ[v] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(processes=c, initializer=_oracle_worker_init, initargs=(tmp.name,)) as pool:
+            pool.map(_oracle_worker_filter, [(j, j + 1, 1) for j in range(c)])  # load, warm up
+            its_sample = 1
+            t0 = time.perf_counter()
+            its = sum(pool.map(_oracle_worker_filter, [(j, j + 1, its_sample) for j in range(c)]))
+            t1 = time.perf_counter() - t0
+            its_sample = int(max(1, min(it_max, (budget_s * 0.6) / max(t1, 1e-3))))
+            t0 = time.perf_counter()
+            its = sum(pool.map(_oracle_worker_filter, [(j, j + 1, its_sample) for j in range(c)]))
+            t_f = time.perf_counter() - t0
+    finally:
+        for v, old in env_keep.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+        os.unlink(tmp.name)
     per_it = t_f / max(its, 1)
-    est = col_iters * per_it + outer * t_rr
-    return {"value": n_found / est, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle filter apply of {c} of {wl.block} columns x {wl.m} poles x It_max={wl.it_max} "
-                       f"({its} column-iterations, {t_f:.1f} s) + one CholQR2/RR step on the full block "
-                       f"({t_rr:.1f} s), scaled to the GPU solve's {col_iters} column-iterations and "
-                       f"{outer} outer iterations"),
-            "seconds_sampled": t_f + t_rr}
+    # (ii) one outer update on c_rr columns (all cores in BLAS), sparse and dense parts apart
+    A, B = p.A(), p.B()
+    c_rr = min(k, 96)
+    U = np.ascontiguousarray(V1[:, :c_rr])
+    t0 = time.perf_counter()
+    A @ U
+    B @ U
+    B @ U
+    t_sp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Q, _ = orc.cholqr2(U, B)
+    orc.rayleigh_ritz(Q, A)
+    t_rr = time.perf_counter() - t0
+    k_mean = max(1.0, col_solves / max(m * outer, 1))
+    t_step = t_sp * (k_mean / c_rr) + max(t_rr - t_sp, 0.0) * (k_mean / c_rr) ** 2
+    est = col_iters * per_it + outer * t_step
+    return {"value": n_found / est, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle warm-started filter apply of {c} of {k} start columns x {m} poles x {its_sample} COCG "
+                       f"updates ({its} column-iterations in {t_f:.1f} s, one column per process, {c} processes on "
+                       f"{cores} cores) + one Cholesky-QR2/Rayleigh-Ritz step on {c_rr} columns ({t_rr:.1f} s, "
+                       f"BLAS on all cores), scaled to this run's GPU solve: {col_iters} column-iterations and "
+                       f"{outer} outer iterations at a mean active block of {k_mean:.0f}"),
+            "seconds_sampled": t_f + t_rr + t_sp}
+
+
+def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic):
+    """Roofline of the fused shifted SpMM + COCG phase-1 launch (the dominant kernel) at k
+    columns x m poles: algorithmic flops 8 per (entry, complex column) + 32 per (row, complex
+    column), algorithmic bytes 5 complex entries per (row, column) (r, p, q read; p, q
+    written) + one pass over the pattern and both value arrays.  The bound is whichever of
+    the ALU (FP64 / FP32 FMA pipe) and HBM times is larger."""
+    W = m * k
+    es = 16 if precision == 0 else 8
+    flops = 8.0 * p.nnz * W + 32.0 * p.n * W
+    nbytes = 5.0 * es * p.n * W + p.nnz * (4 + 2 * (8 if precision == 0 else 4))
+    hbm, hbm_note = measured_hbm_gbs()
+    alu_peak = FP64_PEAK_TFLOPS if precision == 0 else FP32_PEAK_TFLOPS
+    t_alu = flops / (alu_peak * 1e12)
+    t_hbm = nbytes / (hbm * 1e9)
+    s = spmm_ms / 1e3
+    kern = "cocg_spmm_kernel<double>" if precision == 0 else "cocg_spmm (FP32)"
+    if t_alu >= t_hbm:
+        achieved = flops / s / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": traffic, "kernel": kern,
+                "note": (f"FP{64 if precision == 0 else 32} FMA pipe bound ({flops / nbytes:.1f} flop/B); peak = 152 SMs "
+                         f"x {2 if precision == 0 else 128} FMA/clock x 2 x 2.07 GHz (derived); HBM "
+                         f"{nbytes / s / 1e9:.0f} GB/s = {nbytes / s / 1e9 / hbm:.2f} {hbm_note} {hbm:.0f} GB/s"),
+                "hbm_gbs_algorithmic": nbytes / s / 1e9, "flops_per_launch": flops, "bytes_per_launch": nbytes}
+    achieved = nbytes / s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": kern, "note": f"{hbm_note} hbm_gbs; {flops / s / 1e12:.1f} TFLOP/s",
+            "flops_per_launch": flops, "bytes_per_launch": nbytes}
 
 
 def main():
@@ -180,16 +291,24 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="q1_lap_41")
-    ap.add_argument("--it-max", type=int, default=None)
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--it-max", type=int, default=None, help="It_max of the timed path (default per workload)")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="timed path: 1 = complex-FP32 COCG in FP64 refinement (default), 0 = FP64 throughout")
+    ap.add_argument("--precond", type=int, default=None, help="Jacobi-preconditioned inner solves (default per workload)")
+    ap.add_argument("--group", type=int, default=0, help="rows per group of the COCG SpMM (0 = chosen at setup)")
+    ap.add_argument("--compare-steps", type=int, default=1,
+                    help="timed solves of the other precision on the same workload (0 = skip)")
+    ap.add_argument("--compare-it-max", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=2, help="whole solves from host buffers for the e2e figure")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes of one SpMM launch from an ncu capture of this build (else null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="also write the raw nvidia-smi clock samples of the timed region to this file")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch64: also time the plain FP64 batched solve")
-    ap.add_argument("--mixed-it-max", type=int, default=8,
-                    help="It_max of the complex-FP32 inner solves for the mixed-path line (0 = skip)")
+    ap.add_argument("--mixed-it-max", type=int, default=8, help="batch64 / sens48: It_max of the mixed path")
     ap.add_argument("--dense", type=int, default=1,
                     help="1: FP64-accurate split-bf16 tensor-core products in the outer update; 0: FP64 FMA")
     ap.add_argument("--it-adapt", type=int, default=0,
@@ -223,134 +342,121 @@ def main():
     import slrf_inputs as si
     from paper_2510_17334_gb300 import slrf
 
-    wl, desc = workload(args.workload, args.it_max)
+    prec = args.precision
+    it_main = args.it_max or (DEFAULT_IT_MAX if prec == 1 else DEFAULT_IT_MAX_FP64).get(args.workload, 40)
+    wl, desc = workload(args.workload, it_main)
     p = wl.pencil
-    opts = slrf.slrf_opts_default(m=wl.m, it_max=wl.it_max, precision=args.precision, dense=args.dense)
+    precond = DEFAULT_PRECOND.get(args.workload, 0) if args.precond is None else args.precond
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, opts, stream=stream)
-        V0 = torch.from_numpy(si.start_block(p.n, wl.block, wl.seed)).cuda()
-        found = []
-        last = None
-        for _ in range(args.warmup):
-            last = ctx.solve(V0)
-        stream.synchronize()
 
-        def barrier():
-            if world > 1:
-                torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-        barrier()
-        cp, cf = clocks_start(args.clocks_csv)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        stats = []
-        e0.record(stream)
-        for _ in range(args.steps):
-            rc, nf, ev, X, rs, st = ctx.solve(V0)
-            found.append(nf)
-            stats.append(st)
-            last = (rc, nf, ev, X, rs, st)
-        e1.record(stream)
-        barrier()
-        clk = clocks_stop(cp, cf, local)
-        ms = e0.elapsed_time(e1)
-        total_found, ms_max = reduce_over_ranks(sum(found), ms, world)
-        rc, nf, ev, X, rs, st = last
-        maxres = float(rs.max().item())
-        # kernel-level roofline of the dominant kernel (the fused shifted SpMM + COCG phase 1)
-        tim = ctx.filter_timing(V0[:, :wl.block])
-        # end-to-end through the host-buffer entry point
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        hrp, hcol, hA, hB = pin(p.rowptr), pin(p.col.astype(np.int32)), pin(p.valA), pin(p.valB)
-        hV0 = pin(si.start_block(p.n, wl.block, wl.seed))
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    def timed_solves(precision, it_max, steps, warmup, clocks=False):
+        opts = slrf.slrf_opts_default(m=wl.m, it_max=it_max, precision=precision, dense=args.dense, precond=precond,
+                                      group=args.group)
+        with torch.cuda.stream(stream):
+            ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, opts, stream=stream)
+            V0 = torch.from_numpy(si.start_block(p.n, wl.block, wl.seed)).cuda()
+            for _ in range(warmup):
+                ctx.solve(V0)
+            barrier()
+            cp, cf = clocks_start(args.clocks_csv) if clocks else (None, None)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            found, stats, last = [], [], None
+            e0.record(stream)
+            for _ in range(steps):
+                last = ctx.solve(V0)
+                found.append(last[1])
+                stats.append(last[5])
+            e1.record(stream)
+            barrier()
+            clk = clocks_stop(cp, cf, local) if clocks else None
+            ms = e0.elapsed_time(e1)
+        return ctx, V0, found, stats, last, ms, clk
+
+    # ---- the timed path
+    ctx, V0, found, stats, last, ms, clk = timed_solves(prec, it_main, args.steps, args.warmup, clocks=True)
+    total_found, ms_max = reduce_over_ranks(sum(found), ms, world)
+    rc, nf, ev, X, rs, st = last
+    maxres = float(rs.max().item())
+    # kernel-level roofline of the dominant kernel (the fused shifted SpMM + COCG phase 1)
+    with torch.cuda.stream(stream):
+        tim = ctx.filter_timing(V0[:, :wl.block])
+    ctx.close()
+    spmm_ms = tim["ms_spmm"] / max(tim["n_spmm"], 1)
+    roof = spmm_roofline(p, wl.m, wl.block, prec, spmm_ms, args.traffic_bytes)
+    roof["update_ms"] = tim["ms_update"] / max(tim["n_update"], 1)
+    roof["spmm_ms"] = spmm_ms
+    # ---- the other precision on the same workload (FP64 vs mixed at equal residual)
+    compare = None
+    if args.compare_steps > 0:
+        cprec = 1 - prec
+        cit = args.compare_it_max or (DEFAULT_IT_MAX if cprec == 1 else DEFAULT_IT_MAX_FP64).get(args.workload, 40)
+        cctx, _, cfound, cstats, clast, cms, _ = timed_solves(cprec, cit, args.compare_steps, 0)
+        cctx.close()
+        ctot, cms = reduce_over_ranks(sum(cfound), cms, world)
+        cev = clast[2].cpu().numpy()
+        fev = ev.cpu().numpy()
+        diff = float(np.max(np.abs(cev - fev) / np.abs(fev))) if len(cev) == len(fev) and len(fev) else None
+        compare = {"precision": cprec, "value": ctot / (cms / 1e3), "unit": "eigenpairs/s", "it_max": cit,
+                   "steps": args.compare_steps, "warmup": 0, "ms_per_step": cms / args.compare_steps,
+                   "eigenpairs_found": clast[1], "max_resid": float(clast[4].max().item()) if clast[1] else None,
+                   "max_rel_eig_diff": diff, "outer_iters": clast[5]["outer_iters"],
+                   "ms_filter_per_step": clast[5]["ms_filter"], "ms_dense_per_step": clast[5]["ms_dense"]}
+    # ---- end to end through the host-buffer entry point (setup + solve + copies per step)
+    opts = slrf.slrf_opts_default(m=wl.m, it_max=it_main, precision=prec, dense=args.dense, precond=precond,
+                                  group=args.group)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hrp, hcol, hA, hB = pin(p.rowptr), pin(p.col.astype(np.int32)), pin(p.valA), pin(p.valB)
+    hV0 = pin(si.start_block(p.n, wl.block, wl.seed))
+    e2e_found, e2e_s = 0, 0.0
+    torch.cuda.synchronize()
+    for _ in range(max(1, args.e2e_steps)):
         t0 = time.perf_counter()
         ev_h, X_h, rs_h, st_h = slrf.slrf_solve_host(hrp, hcol, hA, hB, wl.gamma, wl.block, opts, hV0)
-        e2e_s = time.perf_counter() - t0
-        h2d = hrp.nbytes + hcol.nbytes + hA.nbytes + hB.nbytes + hV0.nbytes
-        d2h = ev_h.nbytes * 2 + p.n * wl.block * 8
-        mixed = None
-        if args.precision == 0 and args.mixed_it_max > 0:
-            # the same workload with complex-FP32 inner solves inside the FP64 outer loop
-            mopts = slrf.slrf_opts_default(m=wl.m, it_max=args.mixed_it_max, precision=1)
-            mctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, mopts, stream=stream)
-            for _ in range(args.warmup):
-                mctx.solve(V0)
-            barrier()
-            m0 = torch.cuda.Event(enable_timing=True)
-            m1 = torch.cuda.Event(enable_timing=True)
-            mfound = []
-            m0.record(stream)
-            for _ in range(args.steps):
-                mres = mctx.solve(V0)
-                mfound.append(mres[1])
-            m1.record(stream)
-            barrier()
-            mms = m0.elapsed_time(m1)
-            mev = mres[2].cpu().numpy()
-            fev = ev.cpu().numpy()
-            dev_ = float(np.max(np.abs(mev - fev) / fev)) if len(mev) == len(fev) else None
-            mtot, mms = reduce_over_ranks(sum(mfound), mms, world)
-            mixed = {"value": mtot / (mms / 1e3), "unit": "eigenpairs/s", "it_max": args.mixed_it_max,
-                     "ms_per_step": mms / args.steps, "eigenpairs_found": mres[1],
-                     "max_resid": float(mres[4].max().item()),
-                     "max_rel_eig_diff_vs_fp64": dev_, "outer_iters": mres[5]["outer_iters"],
-                     "ms_filter_per_step": mres[5]["ms_filter"], "ms_dense_per_step": mres[5]["ms_dense"]}
-            mctx.close()
-
+        e2e_s += time.perf_counter() - t0
+        e2e_found += len(ev_h)
+    h2d = hrp.nbytes + hcol.nbytes + hA.nbytes + hB.nbytes + hV0.nbytes
+    d2h = 2 * 8 * wl.block + p.n * wl.block * 8
     value = total_found / (ms_max / 1e3)
     col_solves = sum(s["column_solves"] for s in stats)
     col_iters = sum(s["column_iterations"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    k0 = wl.block
-    nnz, n, m = p.nnz, p.n, wl.m
-    elem = 16 if args.precision == 0 else 8
-    flops_spmm = 8.0 * nnz * m * k0 + 32.0 * n * m * k0
-    bytes_spmm = elem * n * m * k0 * 5 + nnz * (4 + 2 * (8 if args.precision == 0 else 4))
-    spmm_ms = tim["ms_spmm"] / max(tim["n_spmm"], 1)
-    if args.precision == 0:
-        achieved = flops_spmm / (spmm_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": SPMM64_TRAFFIC_Q1_41 if (args.workload == "q1_lap_41" and k0 == 160 and m == 8) else None,
-                "kernel": "cocg_spmm_kernel<double>",
-                "note": ("FP64 FMA pipe bound: 8 flops/nnz/complex column + 32 flops/row/column per launch; "
-                         "peak = 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (measured 1.197 TFLOP/s at 1.98 GHz)"),
-                "hbm_gbs_algorithmic": bytes_spmm / (spmm_ms / 1e3) / 1e9}
-    else:
-        peak = 6701.5
-        achieved = bytes_spmm / (spmm_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "cocg_spmm_kernel<float>", "note": "of measured hbm_gbs"}
+    W = wl.m * wl.block
+    es = 16 if prec == 0 else 8
     line = {
         "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "c32-in-f64",
+        "vs_baseline": None, "dtype": "f64" if prec == 0 else "c32 inner solves in f64 refinement",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}", "it_max": wl.it_max, "precision": args.precision,
-                   "l2": "inputs larger than L2 (COCG state %.1f GB)" % (4 * elem * n * m * k0 / 1e9),
+        "config": {"workload": f"{args.workload}: {desc}", "it_max": it_main, "precision": prec, "precond": precond,
+                   "group": args.group,
+                   "l2": "inputs larger than L2 (COCG state %.1f GB)" % (4 * es * p.n * W / 1e9),
                    "parallelism": f"replicas x{world}"},
         "column_solves_per_s": col_solves * world / (ms_max / 1e3),
         "column_iterations_per_s": col_iters * world / (ms_max / 1e3),
-        "spmm_gbs_algorithmic": bytes_spmm / (spmm_ms / 1e3) / 1e9,
-        "eigenpairs_found": nf, "max_resid": maxres, "outer_iters": st["outer_iters"],
+        "spmm_gbs_algorithmic": roof.get("hbm_gbs_algorithmic", roof["achieved"]),
+        "eigenpairs_found": nf, "eigenpairs_expected": wl.n_expected, "max_resid": maxres, "rc": rc,
+        "outer_iters": st["outer_iters"],
         "ms_filter_per_step": sum(s["ms_filter"] for s in stats) / args.steps,
         "ms_dense_per_step": sum(s["ms_dense"] for s in stats) / args.steps,
         "roofline": roof,
-        "e2e": {"value": len(ev_h) / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_found / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": max(1, args.e2e_steps)},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "mixed_precision": mixed,
+        "compare": compare,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_subprocess(args.workload, wl.it_max, nf, int(col_iters / args.steps),
-                                                       st["outer_iters"])
+        line["cpu_baseline"] = cpu_baseline_subprocess(args.workload, it_main, precond, nf,
+                                                       int(col_iters / args.steps), st["outer_iters"],
+                                                       int(col_solves / args.steps), wl.m)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -531,44 +637,59 @@ def sens_bench(args, rank, world, local):
         print(json.dumps(line))
 
 
-def cpu_baseline_subprocess(name, it_max, n_found, col_iters, outer):
+def cpu_baseline_subprocess(name, it_max, precond, n_found, col_iters, outer, col_solves, m):
+    """cpu_baseline_sample in a fresh process (its pool starts with spawn; no CUDA there)."""
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.cpu_baseline_sample(%r, %d, %d, %d, %d)))" %
-            (ROOT, name, it_max, n_found, col_iters, outer))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+            "print(json.dumps(bench.cpu_baseline_sample(%r, %d, %d, %d, %d, %d, %d, %d)))" %
+            (ROOT, name, it_max, precond, n_found, col_iters, outer, col_solves, m))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
     try:
         return json.loads(r.stdout.strip().splitlines()[-1])
     except Exception:
         return {"value": None, "error": r.stderr[-300:]}
 
 
+def solve_counts(name: str):
+    """Counts of one solve of the workload by Alg. 2 at the timed settings (outer iterations,
+    column-iterations, column-solves, eigenpairs), stored with the workload inputs
+    (slrf_inputs/solve_counts.json); the oracle performs the same counts (the parity tests
+    check identical COCG update counts), so they scale the oracle's timed sample."""
+    path = os.path.join(ROOT, "slrf_inputs", "solve_counts.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh).get(name)
+    except Exception:
+        return None
+
+
 def reference_arm(args, rank, world):
     """The oracle as it stands on the host cores, same workload, metric and unit.  Each step
-    is a bounded sample (cpu_baseline_sample) scaled to one whole solve with the workload's
-    recorded solve counts.  Under torchrun only rank 0 works."""
+    is a bounded sample (cpu_baseline_sample: every core busy) scaled to one whole solve
+    with the workload's solve counts.  Under torchrun only rank 0 works."""
     if rank != 0:
         return
-    wl, desc = workload(args.workload, args.it_max)
-    cnt = SOLVE_COUNTS.get(args.workload)
+    cnt = solve_counts(args.workload)
     if cnt is None:
-        print(json.dumps({"impl": "reference", "unavailable": f"no recorded solve counts for {args.workload}"}))
+        print(json.dumps({"impl": "reference", "unavailable": f"no solve counts recorded for {args.workload}"}))
         return
+    wl, desc = workload(args.workload, cnt["it_max"])
     vals = []
     t_start = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline_sample(args.workload, wl.it_max, cnt["n_found"], cnt["column_iterations"], cnt["outer"],
-                                budget_s=8.0)
+        r = cpu_baseline_sample(args.workload, cnt["it_max"], cnt.get("precond", 0), cnt["n_found"],
+                                cnt["column_iterations"], cnt["outer"], cnt["column_solves"], wl.m, budget_s=6.0)
         if s >= args.warmup:
             vals.append(r)
     v = statistics.median([r["value"] for r in vals])
     line = {"metric": METRIC, "value": v, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": (time.perf_counter() - t_start) * 1e3 / (args.warmup + args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {desc}", "it_max": wl.it_max, "precision": 0},
+            "config": {"workload": f"{args.workload}: {desc}", "it_max": cnt["it_max"],
+                       "precision": cnt.get("precision", 0), "precond": cnt.get("precond", 0),
+                       "l2": "n/a (host)", "parallelism": "replicas x1"},
             "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "eigenpairs/s", "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"].replace("this run's GPU solve", "the recorded solve")},
             "e2e": {"value": v, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

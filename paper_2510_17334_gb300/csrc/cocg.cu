@@ -36,7 +36,7 @@
 #endif
 // grouped-row SpMM: records in flight per warp, resident blocks per SM
 #ifndef SLRF_GRP_UNROLL
-#define SLRF_GRP_UNROLL 4
+#define SLRF_GRP_UNROLL 8
 #endif
 #ifndef SLRF_GRP_MINB
 #define SLRF_GRP_MINB 2
@@ -391,7 +391,7 @@ template <> __device__ __forceinline__ void srec_get<double>(const SRec<double> 
 // (pole, column) in the last block of the tile (breakdown: mu = 0 or not finite).
 template <typename R, int VEC>
 __device__ __forceinline__ void spmm_tail(const CocgArgs<R> &a, const R (&acc)[VEC][2], const int w_tile0,
-                                          const int rb, const int tile) {
+                                          const int rb, const int tile, const int nblocks) {
   constexpr int NQ = 2;
   double out[NQ];
   int w;
@@ -400,7 +400,7 @@ __device__ __forceinline__ void spmm_tail(const CocgArgs<R> &a, const R (&acc)[V
   for (int v = 0; v < VEC; ++v)
 #pragma unroll
     for (int qq = 0; qq < NQ; ++qq) accd[v][qq] = (double)acc[v][qq];
-  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, a.nrb, a.partial, a.counters + tile, out, w))
+  if (!block_then_grid_reduce<VEC, NQ>(accd, a.W, w_tile0, rb, nblocks, a.partial, a.counters + tile, out, w))
     return;
   if (threadIdx.x < 32 * VEC) {
     WScal s = a.ws[w];
@@ -527,7 +527,7 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
       finish_row(i, sa, sb, rv, pv, qv);
     }
   }
-  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile);
+  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
 
 // s = (A - sigma B) r for groups of G consecutive rows that share one union column list
@@ -631,11 +631,16 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
         const unsigned char *rp = rb_ + t * RS;
         const int c = *reinterpret_cast<const int *>(rp + 16 * G);
         const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
+        // the record's 2 G values in G 16-byte broadcast loads
+        float4 rv4[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) rv4[j] = reinterpret_cast<const float4 *>(rp)[j];
+        const float *rvf = reinterpret_cast<const float *>(rv4);
         if constexpr (sizeof(R) == 4) {
 #pragma unroll
           for (int j = 0; j < G; ++j) {
-            const float2 av = *reinterpret_cast<const float2 *>(rp + 8 * j);
-            const float2 bv = *reinterpret_cast<const float2 *>(rp + 8 * (G + j));
+            const float2 av = make_float2(rvf[2 * j], rvf[2 * j + 1]);
+            const float2 bv = make_float2(rvf[2 * (G + j)], rvf[2 * (G + j) + 1]);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
               sa[j][v] = ffma2(av, x.z[v], sa[j][v]);
@@ -643,10 +648,11 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
             }
           }
         } else {
+          const double *rvd = reinterpret_cast<const double *>(rv4);
 #pragma unroll
           for (int j = 0; j < G; ++j) {
-            const double av = *reinterpret_cast<const double *>(rp + 8 * j);
-            const double bv = *reinterpret_cast<const double *>(rp + 8 * (G + j));
+            const double av = rvd[j];
+            const double bv = rvd[G + j];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
               sa[j][v].x = fma(av, x.z[v].x, sa[j][v].x);
@@ -710,7 +716,7 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
       __syncwarp();
     }
   }
-  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile);
+  spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
 
 // ------------------------------------------------------------------------------ residual
@@ -832,9 +838,9 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(c
 template <typename R, int G> __host__ __device__ constexpr int cocg_grp_minb() {
   return G == 1 ? cocg_minb<R>() : SLRF_GRP_MINB;
 }
-template <typename R, bool FIRST, int FM, int G>
-__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, G>())) cocg_dual_kernel(const CocgArgs<R> a, int s0,
-                                                                                       int ns, int u0, int nu) {
+template <typename R, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(const CocgArgs<R> a, int s0, int ns,
+                                                                              int u0, int nu) {
   const int NS = a.nrb * ns, NU = a.nrb * nu;
   const int both = 2 * (NS < NU ? NS : NU);
   const int b = blockIdx.x;
@@ -847,12 +853,8 @@ __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, G>())) cocg_dual_k
     spmm = NS > NU;
     item = (b - both) + (NS < NU ? NS : NU);
   }
-  if (spmm) {
-    if constexpr (G == 1) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
-    else cocg_spmm_grp_body<R, G, false>(a, item % a.nrb, s0 + item / a.nrb);
-  } else {
-    cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
-  }
+  if (spmm) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
+  else cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
 }
 template <typename R, bool FRESH>
 __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_kernel(const CocgArgs<R> a) {
@@ -1087,11 +1089,10 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
   }
 #undef UPD
 }
-template <typename R, int G>
-static void cocg_dual_g(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm, cudaStream_t st) {
+template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
+                                    cudaStream_t st) {
   const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
-  const int smem = G == 1 ? 0 : grp_smem_bytes<G>();
-#define DUAL(F, M) cocg_dual_kernel<R, F, M, G><<<blocks, kThreads, smem, st>>>(a, s0, ns, u0, nu)
+#define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
   if (first) DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
   else {
     switch (fm) {
@@ -1104,22 +1105,11 @@ static void cocg_dual_g(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bo
   }
 #undef DUAL
 }
-template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
-                                    cudaStream_t st) {
-  if constexpr (sizeof(R) == 4) {
-    switch (a.G) {
-      case 2: cocg_dual_g<R, 2>(a, s0, ns, u0, nu, first, fm, st); return;
-      case 3: cocg_dual_g<R, 3>(a, s0, ns, u0, nu, first, fm, st); return;
-      case 4: cocg_dual_g<R, 4>(a, s0, ns, u0, nu, first, fm, st); return;
-      default: break;
-    }
-  }
-  cocg_dual_g<R, 1>(a, s0, ns, u0, nu, first, fm, st);
-}
 template <typename R, int G> static void cocg_spmm_grp(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   if (fresh) cocg_spmm_grp_kernel<R, G, true><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
   else cocg_spmm_grp_kernel<R, G, false><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
 }
+
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   switch (a.G) {
     case 2: cocg_spmm_grp<R, 2>(a, st, fresh); return;
@@ -1137,16 +1127,6 @@ template <typename R, int G> static void grp_attrs() {
   const int sm = grp_smem_bytes<G>();
   cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if constexpr (sizeof(R) == 4) {
-    cudaFuncSetAttribute(cocg_dual_kernel<R, true, kFinalNone, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalNone, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalU, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalStoreD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         sm);
-    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalAddD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cocg_dual_kernel<R, false, kFinalUFromD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         sm);
-  }
 }
 void cocg_kernel_attrs() {
   static bool done = false;

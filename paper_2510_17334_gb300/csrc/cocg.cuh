@@ -133,6 +133,7 @@ template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args,
 // call before the first launch and outside stream capture).
 void cocg_kernel_attrs();
 
+
 // Grouped-row format: cnt[g] = number of distinct columns of rows [G g, G g + G) (grp_count),
 // then the records of every group at the offsets gptr (grp_fill, R = float or double).
 void grp_count(int64_t n, int G, const int64_t *rowptr, const int32_t *col, int *cnt, cudaStream_t st);

@@ -329,7 +329,9 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   const int64_t rblocks = (int64_t)ctx->sm_count * 4;
   int64_t rpb = std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
   if (ctx->rpb_tuned > 0) rpb = std::max<int64_t>(rpb, ctx->rpb_tuned);
-  rpb = (rpb + ctx->grp - 1) / ctx->grp * ctx->grp;  // whole groups per row block
+  // whole groups per row block, the same number for every warp of the block
+  const int64_t unit = (int64_t)ctx->grp * kWarps;
+  rpb = (rpb + unit - 1) / unit * unit;
   const int nrb = (int)((ctx->n + rpb - 1) / rpb);
   CocgArgs<R> a{};
   a.n = ctx->n;
@@ -382,7 +384,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   // the update of the other (cocg_dual); each group still alternates update and SpMM in
   // order.  Measured on the 41^3 workload: -3 % filter time in FP32; in FP64 both kernels
   // load the FP64 pipe (the update does ~11 FP64 FMAs per entry), so there it is not used.
-  const bool dual_ok = sizeof(R) == 4 && T >= 2 && itm >= 2;
+  const bool dual_ok = sizeof(R) == 4 && T >= 2 && itm >= 2 && ctx->grp == 1;
   ctx->launches += 2 * itm + 1 + (sizeof(R) == 4 ? 3 : 0) + (int64_t)(nref - 1) * (2 * itm + 1) +
                    (dual_ok && tm == nullptr ? nref : 0);
   // one launch sequence for the graph, the direct and the timed path; `kind` tags each
