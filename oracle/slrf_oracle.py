@@ -373,3 +373,38 @@ def eig_grad_full(rowptr, col, A, B, evals, X, g_eval, g_X):
     gB = -((X[rows, :] * X[cols, :]) @ (np.asarray(g_eval) * evals + half)
            + (Xi[rows, :] * X[cols, :]) @ np.asarray(evals))
     return gA, gB, Xi
+
+
+# ----------------------------------------------------------------------------------------
+# O-result at full size: the plain definition of the answer (the eigenpairs in (0, gamma]),
+# from library routines rather than from the method (used to pin large workloads)
+# ----------------------------------------------------------------------------------------
+def shift_invert_spectrum(A, B, k: int, tol: float = 1e-12):
+    """The k smallest eigenvalues of A x = lambda B x (A, B sparse SPD), ascending, by
+    shift-invert Lanczos at sigma = 0 (ARPACK through scipy.sparse.linalg.eigsh, with a
+    sparse LU of A from SuperLU)."""
+    import scipy.sparse.linalg as spla
+
+    A = sp.csc_matrix(A)
+    B = sp.csc_matrix(B)
+    lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", options=dict(SymmetricMode=True))
+    op = spla.LinearOperator(A.shape, matvec=lu.solve, dtype=np.float64)
+    vals = spla.eigsh(A, k=k, M=B, sigma=0.0, which="LM", OPinv=op, return_eigenvectors=False, tol=tol)
+    return np.sort(vals)
+
+
+def inertia_count(A, B, gamma: float):
+    """Number of eigenvalues below gamma of the pencil (A, B) by Sylvester's law of inertia:
+    the negative pivots of a symmetric factorisation P (A - gamma B) P^T = L D L^T.  SuperLU
+    in symmetric mode with diagonal pivoting only (diag_pivot_thresh = 0) factors
+    P M P^T = L U with U = D L^T for the symmetric M, so the signs of U's diagonal are those
+    of D.  Returns (count, ok): ok is False when the row and column orderings differ (the
+    factorisation is then not congruent and the count is not trusted)."""
+    import scipy.sparse.linalg as spla
+
+    M = sp.csc_matrix(A - gamma * B)
+    lu = spla.splu(M, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                   options=dict(SymmetricMode=True))
+    ok = bool(np.array_equal(lu.perm_r, lu.perm_c))
+    d = lu.U.diagonal()
+    return int(np.sum(d < 0)), ok

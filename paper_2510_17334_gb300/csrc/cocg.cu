@@ -76,6 +76,42 @@ template <typename R> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<
   }
 }
 
+// Streaming (evict-first) loads and stores of the SpMM's own-row p and q: they are read
+// and written once per launch, so they should not push the gathered rows of r out of L2.
+#ifndef SLRF_SPMM_STREAM
+#define SLRF_SPMM_STREAM 1
+#endif
+template <typename R> __device__ __forceinline__ Vec<R> ldv_cs(const cx_t<R> *p) {
+  if constexpr (SLRF_SPMM_STREAM == 0) {
+    return ldv<R>(p);
+  } else {
+    Vec<R> v;
+    if constexpr (sizeof(R) == 8) {
+      v.z[0] = __ldcs(reinterpret_cast<const double2 *>(p));
+    } else {
+#pragma unroll
+      for (int j = 0; j < SLRF_F32_VEC / 2; ++j) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p) + j);
+        v.z[2 * j] = make_float2(t.x, t.y);
+        v.z[2 * j + 1] = make_float2(t.z, t.w);
+      }
+    }
+    return v;
+  }
+}
+template <typename R> __device__ __forceinline__ void stv_cs(cx_t<R> *p, const Vec<R> &v) {
+  if constexpr (SLRF_SPMM_STREAM == 0) {
+    stv<R>(p, v);
+  } else if constexpr (sizeof(R) == 8) {
+    __stcs(reinterpret_cast<double2 *>(p), v.z[0]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < SLRF_F32_VEC / 2; ++j)
+      __stcs(reinterpret_cast<float4 *>(p) + j,
+             make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y));
+  }
+}
+
 template <typename R> __device__ __forceinline__ cx_t<R> to_c(double2 a) {
   cx_t<R> z; z.x = (R)a.x; z.y = (R)a.y; return z;
 }
@@ -508,15 +544,15 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
         acc[v][0] += pn.x * qn.x - pn.y * qn.y;
         acc[v][1] += pn.x * qn.y + pn.y * qn.x;
       }
-      stv<R>(a.p + off, pv);
-      stv<R>(a.q + off, qv);
+      stv_cs<R>(a.p + off, pv);
+      stv_cs<R>(a.q + off, qv);
     };
     auto load_own = [&](int64_t i, Vec<R> &rv, Vec<R> &pv, Vec<R> &qv) {
       const size_t off = (size_t)i * a.W + w0;
       rv = ldv<R>(a.r + off);
       if (!FRESH) {
-        pv = ldv<R>(a.p + off);
-        qv = ldv<R>(a.q + off);
+        pv = ldv_cs<R>(a.p + off);
+        qv = ldv_cs<R>(a.q + off);
       }
     };
     for (int64_t i = i0 + warp; i < i1; i += kWarps) {
@@ -673,8 +709,8 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
             const Vec<R> rv = ldv<R>(a.r + off);
             Vec<R> pv, qv;
             if (!FRESH) {
-              pv = ldv<R>(a.p + off);
-              qv = ldv<R>(a.q + off);
+              pv = ldv_cs<R>(a.p + off);
+              qv = ldv_cs<R>(a.q + off);
             }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
@@ -686,8 +722,8 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
               acc[v][0] += pn.x * qn.x - pn.y * qn.y;
               acc[v][1] += pn.x * qn.y + pn.y * qn.x;
             }
-            stv<R>(a.p + off, pv);
-            stv<R>(a.q + off, qv);
+            stv_cs<R>(a.p + off, pv);
+            stv_cs<R>(a.q + off, qv);
           }
 #pragma unroll
           for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }

@@ -273,12 +273,12 @@ static int build_groups(slrf_ctx *ctx, int G) {
 }
 // Candidate G from the pattern.  FP64: the SpMM is bound by the FP64 pipe, so only groups
 // that add no zero products qualify (union x rows == entries), the largest such G.  FP32:
-// a cost model per row of one warp tile (64 complex entries): a gathered row costs its
-// L1 traffic (512 B, ~4 cycles) or the packed FMAs it feeds (8 G per lane, 2 G cycles),
-// whichever is larger; plain CSR pays ~4.6 cycles per entry (gather plus shuffles).
+// a cost per row, in units of one plain-CSR entry, fitted to GB300 timings of the 41^3
+// Laplacian (27 entries/row) and the 64x64x32 elasticity box (81): a record of a G-row
+// group costs about 1.2 + 0.25 G entries (the gather, the staged record, 8 G packed FMAs).
 static int choose_group(slrf_ctx *ctx, int &G) {
   G = 1;
-  double best = (double)ctx->nnz / ctx->n * 4.6;
+  double best = (double)ctx->nnz / ctx->n;
   for (int g = (ctx->mixed ? 2 : 4); ctx->mixed ? g <= 4 : g >= 2; g += ctx->mixed ? 1 : -1) {
     std::vector<int> cnt;
     int rc = group_counts(ctx, g, cnt);
@@ -292,7 +292,7 @@ static int choose_group(slrf_ctx *ctx, int &G) {
       if (slots <= (double)ctx->nnz) { G = g; return SLRF_OK; }
       continue;
     }
-    const double cost = recs / ctx->n * std::max(4.0, 2.0 * g);
+    const double cost = recs / ctx->n * (1.2 + 0.25 * g);
     if (cost < best) { best = cost; G = g; }
   }
   return SLRF_OK;

@@ -141,6 +141,27 @@ def test_full_size_sampled_columns(slrf_mod):
     ctx.close()
 
 
+@pytest.mark.parametrize("warm", [False, True])
+def test_full_size_fp32_filter_sampled_columns(slrf_mod, warm):
+    """41^3 Q1 Laplacian, 160 columns x 8 poles (W = 1,280), the mixed path as the bench runs
+    it (It_max 8, plain CSR SpMM with the two-group schedule, one SpMM tile group beside the
+    other group's update): sampled columns against the FP64 oracle, element by element, at
+    FP32 accuracy times the filter's weight growth (sum |w_j| ~ 20): 5e-3 of max |U|."""
+    wl = si.q1_lap(41)
+    p = wl.pencil
+    it = 8
+    opts = slrf_mod.slrf_opts_default(it_max=it, precision=1, group=1)
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, opts)
+    V1 = si.start_block(p.n, wl.block, wl.seed)
+    th = np.linspace(0.02, 1.3, wl.block) * wl.gamma if warm else None
+    U = ctx.filter_apply(torch.from_numpy(V1), None if th is None else torch.from_numpy(th)).cpu().numpy()
+    ctx.close()
+    so, wo = orc.slrf_poles(8, wl.gamma)
+    cols = [0, 63, 64, 159]
+    Uo, _ = orc.filter_apply(p.A(), p.B(), V1[:, cols], None if th is None else th[cols], so, wo, it, 1e-10)
+    assert np.all(np.abs(U[:, cols] - Uo) <= 5e-3 * np.abs(Uo).max())
+
+
 def test_mixed_refinement_converges_to_the_fp64_filter(slrf_mod):
     """FP64 iterative refinement around complex-FP32 COCG (refine_max steps): with inner
     solves long enough to converge, the filter approaches the oracle's exactly-solved FP64

@@ -244,6 +244,22 @@ def test_solve_q1_41_full_size(slrf_mod):
     assert np.abs(X.T @ (B @ X) - np.eye(105)).max() <= 1e-11
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_q1_41_at_the_benched_settings(slrf_mod, precision):
+    """The 41^3 workload at It_max 8, the inner-solve length its bench line uses, in FP64 and
+    in the mixed path: all 105 eigenpairs against the tensor-product closed form (1e-10 FP64,
+    1e-8 mixed, with the constant-mode floor), residuals <= 1e-8, B-orthonormal vectors."""
+    wl = si.q1_lap(41)
+    rc, nf, ev, X, rs, st = _solve(slrf_mod, wl.pencil, wl.gamma, wl.block, wl.seed, it_max=8, precision=precision)
+    lam = pins.q1_neumann_eigs((41, 41, 41), 1e-3)
+    tol = 1e-10 if precision == 0 else 1e-8
+    assert rc == 0 and nf == 105 == int(np.sum(lam <= wl.gamma))
+    assert np.all(np.abs(ev - lam[:105]) <= np.maximum(tol * lam[:105], 1e-9 * lam[0]))
+    assert rs.max() <= 1e-8
+    B = wl.pencil.B()
+    assert np.abs(X.T @ (B @ X) - np.eye(105)).max() <= 1e-10
+
+
 def test_solve_with_refinement_steps(slrf_mod):
     """Mixed path with two FP64 refinement steps per filter apply: same eigenpairs."""
     nodes = (9, 9, 9)

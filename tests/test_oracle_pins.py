@@ -468,3 +468,25 @@ def test_eigenvector_adjoint_matches_finite_differences():
                 vals.append(c @ lp + np.sum(D * Xp))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - grad @ dv) <= 1e-5 * abs(fd), (which, fd, grad @ dv)
+
+
+def test_full_size_reference_routines_on_a_reduced_box():
+    """The routines that give the full-size elasticity box its reference spectrum and count
+    (shift-invert Lanczos; Sylvester inertia from a symmetric sparse LU), checked on an
+    8 x 8 x 4 box of the same generator (z = 0 clamped, lognormal modulus) against dense
+    eigh and the Bunch-Kaufman inertia; the oracle's Alg. 2 finds the same count there
+    (Jacobi-preconditioned inner solves of It_max 30: unpreconditioned solves of that length
+    leave this lognormal-modulus box unresolved after 40 outer steps)."""
+    E = np.exp(np.random.default_rng(3).normal(0, 0.5, 7 * 7 * 3))
+    p = si.q1_elasticity((8, 8, 4), E=E)
+    A, B = p.A(), p.B()
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    assert np.max(np.abs(orc.shift_invert_spectrum(A, B, 30) - lam[:30]) / lam[:30]) <= 1e-11
+    for want in (10, 30, 100):
+        gamma, cnt = pins.gap_gamma(lam, want)
+        c, ok = orc.inertia_count(A, B, gamma)
+        assert ok and c == cnt == pins.dense_inertia_count(A, B, gamma)
+    gamma, cnt = pins.gap_gamma(lam, 20)
+    r = orc.enhanced_slrf(A, B, gamma, si.start_block(p.n, 30, 3), m=8, it_max=30, outer_max=60, precond=True)
+    assert r.status == orc.OK and len(r.evals) == cnt
+    assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
