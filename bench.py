@@ -31,8 +31,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DEFAULT_WORKLOAD = "elast_64"
 # It_max of the timed solves per workload (swept on GB300; see the design notes): (mixed, FP64)
-DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 20, "bar1d_2000": 200}
-DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 20, "bar1d_2000": 200}
+DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 30, "bar1d_2000": 200}
+DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 30, "bar1d_2000": 200}
 # Jacobi preconditioner on by default for the elasticity boxes (reading R18)
 DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
 
@@ -285,6 +285,66 @@ def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic):
             "flops_per_launch": flops, "bytes_per_launch": nbytes}
 
 
+def paper_table_records(slrf, si, torch):
+    """Two small-problem records on the Q1 Laplacian with 21^3 nodes (n = 9,261, gamma
+    enclosing about 100 eigenvalues, block 1.5x, m = 8, FP64), analogues of the paper's:
+      * Table 3: enhanced Alg. 2 (locking, warm start, It_max 8) against the basic Alg. 1
+        (no locking, zero initial guesses, inner solves to 1e-13 or 2000 updates) -- the
+        time ratio of the two whole solves;
+      * Table 1 "Ratio": per-pole spread of the COCG updates needed to reach 1e-10 from the
+        zero guess (start block, up to 5000 updates) for the SLRF poles and for the
+        midpoint / Gauss-Legendre / Gauss-Chebyshev contour filters (pole tables through
+        slrf_opts.poles), max/min over poles of the mean updates, and each table's whole
+        enhanced solve."""
+    import numpy as np
+
+    wl = si.q1_lap(21)
+    p = wl.pencil
+    V0 = torch.from_numpy(si.start_block(p.n, wl.block, wl.seed)).cuda()
+
+    def solve(**kw):
+        ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block, slrf.slrf_opts_default(**kw))
+        ctx.solve(V0, check=False)  # warm-up (graph capture, module loading)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, nf, ev, X, rs, st = ctx.solve(V0, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ctx.close()
+        return {"rc": rc, "eigenpairs": nf, "outer_iters": st["outer_iters"], "seconds": dt,
+                "column_iterations": st["column_iterations"],
+                "max_resid": float(rs.max().item()) if nf else None}
+
+    enh = solve(it_max=8)
+    basic = solve(it_max=2000, tol_inner=1e-13, lock=0, warm_start=0, outer_max=60)
+    t3 = {"workload": f"q1_lap_21: 3D Q1 Laplacian 21^3 nodes (n={p.n}), gamma={wl.gamma:.4f} "
+                      f"({wl.n_expected} eigenpairs), block {wl.block}, m=8, FP64",
+          "enhanced_alg2": enh, "basic_alg1": basic,
+          "time_ratio_basic_over_enhanced": basic["seconds"] / enh["seconds"]}
+    t1 = {}
+    for rule in ("slrf", "midpoint", "gauss_legendre", "gauss_chebyshev"):
+        kw = {}
+        if rule != "slrf":
+            s_, w_ = slrf.quadrature_table(rule, 8, wl.gamma)
+            kw = {"poles": s_, "weights": w_}
+        ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, wl.block,
+                           slrf.slrf_opts_default(it_max=5000, **kw))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.filter_apply(V0)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        its, rr, bk = ctx.filter_stats(wl.block)
+        ctx.close()
+        per_pole = its.mean(axis=1)
+        rec = {"per_pole_mean_updates": [float(x) for x in per_pole],
+               "ratio_max_over_min": float(per_pole.max() / per_pole.min()),
+               "converged_columns": int(np.sum(rr <= 1e-10)), "filter_seconds": tf,
+               "enhanced_solve": solve(it_max=8, **kw)}
+        t1[rule] = rec
+    return {"alg1_vs_alg2": t3, "pole_tables": t1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +364,8 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes of one SpMM launch from an ncu capture of this build (else null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tables", action="store_true",
+                    help="skip the small-problem records of the paper's Tables 1 and 3")
     ap.add_argument("--clocks-csv", default=None,
                     help="also write the raw nvidia-smi clock samples of the timed region to this file")
     ap.add_argument("--compare-fp64", action="store_true",
@@ -451,6 +513,8 @@ def main():
         "clocks": clk,
         "compare": compare,
     }
+    if rank == 0 and world == 1 and not args.no_tables:
+        line["paper_tables"] = paper_table_records(slrf, si, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args.workload, it_main, precond, nf,
                                                        int(col_iters / args.steps), st["outer_iters"],

@@ -295,6 +295,16 @@ int slrf_tsgram(int64_t n, const double *X, int ldx, int k1, const double *Y, in
 int slrf_tsgemm(int64_t n, const double *X, int ldx, int k1, const double *S, int lds, int k2, double *Z,
                 int ldz, double alpha, double beta, int mode, void *stream);
 
+/* Diagnostic of the library's bounded device-side waits (the paper has no counterpart):
+ * launches one wait that cannot complete -- kind 0: the grid barrier of the Rayleigh-Ritz
+ * eigensolver expecting one block more than the launch has (gives up after 2^22 polls);
+ * kind 1: an mbarrier phase that nothing arrives at (gives up after 2 s, as the bulk-copy
+ * and tensor-core pipelines do) -- and returns SLRF_ETIMEOUT when the wait gave up and
+ * reported it, as it must; the device stays usable.  Allocates and frees 16 bytes,
+ * synchronises the stream (a cudaStream_t or NULL).  Errors: SLRF_EINVAL (kind),
+ * SLRF_ENOMEM, SLRF_ECUDA; SLRF_OK would mean the wait did not report. */
+int slrf_wait_selftest(int kind, void *stream);
+
 /* Release the context and all its device memory.  NULL is accepted. */
 void slrf_destroy(slrf_ctx *ctx);
 

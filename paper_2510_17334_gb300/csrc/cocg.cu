@@ -261,9 +261,17 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
 // ------------------------------------------------------------------------------ update
 // d += alpha p (d = alpha p on the first step); r -= alpha q; reduce rho' and ||r||^2.
 // With final_acc, also U[i][c] = coefV[c] V[i][c] + sum_j 2 Re(w_j d_j).
+// kAccU / kAccUEnd (the updates of a solve without refinement): no d at all -- the filter
+// is linear in d, so each update adds the pole sum of its step to a real accumulator,
+//   Uacc[i][c] (+)= sum_j 2 Re(w_j alpha_j p_j)     (working precision, scaled units),
+// n x k reals instead of d's n x k x m complex entries read and written every update.
+// Uacc is laid out tile by tile ([tile][row][columns of the tile]) so that each launch
+// streams it; the last update (kAccUEnd) writes U = coefV V + Uacc / gscale * dsc in FP64.
 template <typename R, bool FIRST, int FM>
 __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int rb, const int tile) {
-  constexpr bool FINAL = FM != kFinalNone;
+  constexpr bool ACCU_END = FM == kAccUEnd;
+  constexpr bool ACCU = FM == kAccU || ACCU_END;
+  constexpr bool FINAL = FM != kFinalNone && !ACCU;
   constexpr int VEC = cocg_vec<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -290,21 +298,45 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   const int lanes_per_col = a.mp >= VEC ? a.mp / VEC : 1;
+  const bool warp_act = __any_sync(0xffffffffu, any_act);
+  const int cpt = 32 * VEC / a.mp;  // columns of a tile (kAccU accumulator layout)
   for (int64_t i = i0 + warp; i < i1; i += kWarps) {
     const size_t off = (size_t)i * a.W + w0;
     Vec<R> dv;
-    if (FIRST) {
+    R step[VEC];  // kAccU: 2 Re(w_j alpha_j p_j) of this lane's entries
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) dv.z[v] = cmake<C>(0, 0);
-    } else if (any_act || FINAL) {
-      dv = ldv<R>(a.d + off);
+    for (int v = 0; v < VEC; ++v) step[v] = R(0);
+    // kAccU: this lane's accumulator entries (one per column it leads), loaded up front so
+    // that the load overlaps the loads of p, q and r
+    R uold[VEC];
+    R *const uacc = reinterpret_cast<R *>(a.uacc) + ((size_t)tile * a.n + i) * cpt - (size_t)tile * cpt;
+    if constexpr (ACCU) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        uold[v] = R(0);
+        const int c = (w0 + v) / a.mp;
+        const bool lead = a.mp >= VEC ? (v == 0 && (lane % lanes_per_col) == 0) : true;
+        if (!FIRST && (warp_act || ACCU_END) && lead && c < a.k) uold[v] = uacc[c];
+      }
+    } else {
+      if (FIRST) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dv.z[v] = cmake<C>(0, 0);
+      } else if (any_act || FINAL) {
+        dv = ldv<R>(a.d + off);
+      }
     }
     if (any_act) {
       Vec<R> pv = ldv<R>(a.p + off), qv = ldv<R>(a.q + off), rv = ldv<R>(a.r + off);
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         if (act[v]) {
-          dv.z[v] = cfma(al[v], pv.z[v], dv.z[v]);
+          if constexpr (ACCU) {
+            const C ap = cmul(al[v], pv.z[v]);
+            step[v] = R(2) * ((R)wt[v].x * ap.x - (R)wt[v].y * ap.y);
+          } else {
+            dv.z[v] = cfma(al[v], pv.z[v], dv.z[v]);
+          }
           rv.z[v] = cfms(al[v], qv.z[v], rv.z[v]);
         }
         const C rr = rv.z[v];
@@ -313,6 +345,36 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         acc[v][2] += rr.x * rr.x + rr.y * rr.y;
       }
       stv<R>(a.r + off, rv);
+    }
+    if constexpr (ACCU) {
+      if (FIRST || ACCU_END || warp_act) {
+        // pole sum of the step into the accumulator; the last update forms U in FP64
+        auto put = [&](int c, R acc_new) {
+          if (ACCU_END) {
+            double corr = (double)acc_new;
+            if (a.gscale != nullptr) corr /= a.gscale[c];
+            if (a.dsc != nullptr) corr *= a.dsc[i];
+            a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + corr;
+          } else {
+            uacc[c] = acc_new;
+          }
+        };
+        if (a.mp >= VEC) {
+          R sum = R(0);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) sum += step[v];
+          for (int o = lanes_per_col >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          const int c = w0 / a.mp;
+          if ((lane % lanes_per_col) == 0 && c < a.k) put(c, uold[0] + sum);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const int c = (w0 + v) / a.mp;
+            if (c < a.k) put(c, uold[v] + step[v]);
+          }
+        }
+      }
+      continue;
     }
     if (FIRST || any_act) stv<R>(a.d + off, dv);
     if (FM == kFinalStoreD || FM == kFinalAddD) {
@@ -1112,6 +1174,8 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
       case kFinalU: UPD(true, kFinalU); break;
       case kFinalStoreD: UPD(true, kFinalStoreD); break;
       case kFinalAddD: UPD(true, kFinalAddD); break;
+      case kAccU: UPD(true, kAccU); break;
+      case kAccUEnd: UPD(true, kAccUEnd); break;
       default: UPD(true, kFinalUFromD); break;
     }
   } else {
@@ -1120,6 +1184,8 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
       case kFinalU: UPD(false, kFinalU); break;
       case kFinalStoreD: UPD(false, kFinalStoreD); break;
       case kFinalAddD: UPD(false, kFinalAddD); break;
+      case kAccU: UPD(false, kAccU); break;
+      case kAccUEnd: UPD(false, kAccUEnd); break;
       default: UPD(false, kFinalUFromD); break;
     }
   }
@@ -1129,13 +1195,17 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
                                     cudaStream_t st) {
   const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
 #define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
-  if (first) DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
-  else {
+  if (first) {
+    if (fm == kAccU) DUAL(true, kAccU);
+    else DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
+  } else {
     switch (fm) {
       case kFinalNone: DUAL(false, kFinalNone); break;
       case kFinalU: DUAL(false, kFinalU); break;
       case kFinalStoreD: DUAL(false, kFinalStoreD); break;
       case kFinalAddD: DUAL(false, kFinalAddD); break;
+      case kAccU: DUAL(false, kAccU); break;
+      case kAccUEnd: DUAL(false, kAccUEnd); break;
       default: DUAL(false, kFinalUFromD); break;
     }
   }
@@ -1207,6 +1277,8 @@ template <typename R> void cocg_update_batched_launch(const CocgArgs<R> *args, c
       case kFinalU: UPD(true, kFinalU); break;
       case kFinalStoreD: UPD(true, kFinalStoreD); break;
       case kFinalAddD: UPD(true, kFinalAddD); break;
+      case kAccU: UPD(true, kAccU); break;
+      case kAccUEnd: UPD(true, kAccUEnd); break;
       default: UPD(true, kFinalUFromD); break;
     }
   } else {
@@ -1215,6 +1287,8 @@ template <typename R> void cocg_update_batched_launch(const CocgArgs<R> *args, c
       case kFinalU: UPD(false, kFinalU); break;
       case kFinalStoreD: UPD(false, kFinalStoreD); break;
       case kFinalAddD: UPD(false, kFinalAddD); break;
+      case kAccU: UPD(false, kAccU); break;
+      case kAccUEnd: UPD(false, kAccUEnd); break;
       default: UPD(false, kFinalUFromD); break;
     }
   }

@@ -79,6 +79,8 @@ struct CocgArgs {
   // D^-1/2 A D^-1/2 and D^-1/2 B D^-1/2, g is D^-1/2 g, and dsc[i] = D_ii^-1/2 turns the
   // scaled solutions back (y = D^-1/2 z) in the pole sum; null: no preconditioner
   const double *dsc;
+  // kAccU accumulator: [tile][row][32 VEC / mp columns] of R (n x kpad entries)
+  void *uacc;
 };
 
 // Record size of the grouped-row SpMM: 2 G values of 8 bytes and the column, rounded up to 16.
@@ -91,7 +93,11 @@ constexpr int kGrpChunk = SLRF_GRP_CHUNK;  // records per staged chunk (one bulk
 template <int G> __host__ __device__ constexpr int grp_smem_bytes() { return kWarps * 2 * kGrpChunk * grec_bytes<G>(); }
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.
-enum FinalMode { kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, kFinalUFromD = 4 };
+// kAccU: an update of a solve without refinement adds its step to the accumulator (no d
+// array); kAccUEnd: the last one, which also writes U.
+enum FinalMode {
+  kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, kFinalUFromD = 4, kAccU = 5, kAccUEnd = 6
+};
 
 // Launchers (defined in cocg.cu).  All enqueue on `st`.
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);

@@ -247,6 +247,30 @@ void validate_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *
   validate_csr_kernel<<<blocks, 256, 0, st>>>(n, nnz, rowptr, col, flag);
 }
 
+// Diagnostic of the bounded waits (no counterpart in the paper): one wait that cannot
+// complete -- kind 0: the grid barrier expecting one more block than the launch has;
+// kind 1: an mbarrier phase that nothing arrives at.  Each gives up at its limit, sets
+// *err and returns.
+__global__ void wait_selftest_kernel(int kind, unsigned *count, int *err) {
+  if (kind == 0) {
+    GridBarrier gb{count, err};
+    unsigned epoch = 0;
+    grid_sync(gb, gridDim.x + 1u, epoch);
+  } else {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, err, 1);
+    __syncthreads();
+  }
+}
+void wait_selftest(int kind, unsigned *count, int *err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(kind, count, err);
+}
+
 __global__ void row_scale_kernel(int64_t n, int k, const double *__restrict__ s, double *X, int ldx) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;

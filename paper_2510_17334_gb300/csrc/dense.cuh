@@ -25,6 +25,9 @@ void jacobi_scaling(int64_t n, const int64_t *rowptr, const int32_t *col, const 
 // non-decreasing, rowptr[n] = nnz, 0 <= col < n; sets *flag = 1 otherwise (grid of blocks x 256).
 void validate_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, int *flag, int blocks,
                   cudaStream_t st);
+// One bounded wait that cannot complete (kind 0: grid barrier, 1: mbarrier); sets *err.
+// count and err: zeroed device words.
+void wait_selftest(int kind, unsigned *count, int *err, cudaStream_t st);
 // X[i][:] *= s[i] (row-major n x k, leading dimension ldx).
 void row_scale(int64_t n, int k, const double *s, double *X, int ldx, cudaStream_t st);
 

@@ -80,6 +80,7 @@ struct slrf_ctx {
   double *gscale = nullptr;          // FP32 path: per-column right-hand-side scale
   unsigned long long *gmax = nullptr;
   double2 *D64 = nullptr;            // FP32 path with refinement: FP64 correction [n][Wmax]
+  double *uacc = nullptr;            // filter accumulator of the updates without refinement [n][Wmax/mp]
   double *r00 = nullptr;             // ||r0||^2 of the first refinement step, per w
   int last_k = 0, last_W = 0;
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
@@ -348,6 +349,7 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   a.grec = ctx->grec;
   a.err = ctx->iflags + 15;
   a.dsc = ctx->dsc;
+  a.uacc = ctx->uacc;
   a.W = W; a.k = k; a.m = ctx->m; a.mp = ctx->mp;
   a.rows_per_block = (int)rpb; a.nrb = nrb;
   a.d = (cx_t<R> *)ctx->cd; a.r = (cx_t<R> *)ctx->cr; a.p = (cx_t<R> *)ctx->cp; a.q = (cx_t<R> *)ctx->cq;
@@ -399,19 +401,25 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
         if constexpr (sizeof(R) == 4) launch(0, [&] { cocg_residual<R>(a, s); });
         launch(1, [&] { cocg_spmm<R>(a, s, true); });
       }
-      const int fm_last = nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+      // FP32 without refinement: every update adds its step to the accumulator (kAccU, no d
+      // array); in FP64 the extra complex product per entry costs more on the FP64 pipe than
+      // the d traffic it saves, so the FP64 path keeps d
+      const bool accu = nref == 1 && sizeof(R) == 4;
+      const int fm_mid = accu ? kAccU : kFinalNone;
+      const int fm_last = accu ? kAccUEnd
+                               : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
       if (dual && dual_ok) {
         const int n0 = T / 2, n1 = T - n0;  // group 0: tiles [0, n0), group 1: [n0, T)
-        launch(2, [&] { cocg_update<R>(a, true, kFinalNone, s, 0, n0); });  // U_1 of group 0
+        launch(2, [&] { cocg_update<R>(a, true, fm_mid, s, 0, n0); });  // U_1 of group 0
         for (int t = 1; t < itm; ++t) {
           // S_t of group 0 with U_t of group 1, then S_t of group 1 with U_{t+1} of group 0
-          launch(4, [&] { cocg_dual<R>(a, 0, n0, n0, n1, t == 1, kFinalNone, s); });
-          launch(4, [&] { cocg_dual<R>(a, n0, n1, 0, n0, false, t + 1 == itm ? fm_last : kFinalNone, s); });
+          launch(4, [&] { cocg_dual<R>(a, 0, n0, n0, n1, t == 1, fm_mid, s); });
+          launch(4, [&] { cocg_dual<R>(a, n0, n1, 0, n0, false, t + 1 == itm ? fm_last : fm_mid, s); });
         }
         launch(2, [&] { cocg_update<R>(a, false, fm_last, s, n0, n1); });  // U_itm of group 1
       } else {
         for (int it = 1; it <= itm; ++it) {
-          launch(2, [&] { cocg_update<R>(a, it == 1, it == itm ? fm_last : kFinalNone, s); });
+          launch(2, [&] { cocg_update<R>(a, it == 1, it == itm ? fm_last : fm_mid, s); });
           if (it < itm) launch(1, [&] { cocg_spmm<R>(a, s); });
         }
       }
@@ -731,9 +739,13 @@ static void batch_cocg(slrf_batch *b, int P, int total, int nref, int itm, cudaS
       if constexpr (sizeof(R) == 4) cocg_residual_batched_launch<R>(args, pre, P, total, s);
       cocg_spmm_batched_launch<R>(args, pre, P, total, true, s);
     }
-    const int fm_last = nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+    // as in the single-problem schedule: FP32 without refinement accumulates every update's step
+    const bool accu = nref == 1 && sizeof(R) == 4;
+    const int fm_mid = accu ? kAccU : kFinalNone;
+    const int fm_last = accu ? kAccUEnd
+                             : nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
     for (int it = 1; it <= itm; ++it) {
-      cocg_update_batched_launch<R>(args, pre, P, total, it == 1, it == itm ? fm_last : kFinalNone, s);
+      cocg_update_batched_launch<R>(args, pre, P, total, it == 1, it == itm ? fm_last : fm_mid, s);
       if (it < itm) cocg_spmm_batched_launch<R>(args, pre, P, total, false, s);
     }
   }
@@ -815,6 +827,28 @@ int slrf_opts_default(slrf_opts *o) {
   o->seed = 1;
   o->dense = 1;
   return SLRF_OK;
+}
+
+int slrf_wait_selftest(int kind, void *stream) {
+  if (kind < 0 || kind > 1) return SLRF_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  void *buf = nullptr;
+  if (cudaMalloc(&buf, 16) != cudaSuccess) {
+    cudaGetLastError();
+    return SLRF_ENOMEM;
+  }
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
+  if (e == cudaSuccess) {
+    wait_selftest(kind, reinterpret_cast<unsigned *>(buf), reinterpret_cast<int *>(buf) + 1, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, reinterpret_cast<int *>(buf) + 1, sizeof(int),
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return SLRF_ECUDA;
+  return herr != 0 ? SLRF_ETIMEOUT : SLRF_OK;
 }
 
 const char *slrf_strerror(int s) {
@@ -957,7 +991,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
   const size_t refine = (ctx->mixed && o.refine_max > 1) ? 16 * (size_t)n * ctx->Wmax : 0;
-  const size_t need = (state + blocks + matrix + refine) + 8 * partial + (64u << 20);
+  const size_t uacc = 8 * (size_t)n * (ctx->Wmax / ctx->mp);
+  const size_t need = (state + blocks + matrix + refine + uacc) + 8 * partial + (64u << 20);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(SLRF_ECUDA);
   if (need > fr) return fail(SLRF_ENOMEM);
@@ -1063,6 +1098,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
     AL(ctx->D64, (size_t)n * ctx->Wmax);
     AL(ctx->r00, ctx->Wmax);
   }
+  AL(ctx->uacc, (size_t)n * (ctx->Wmax / ctx->mp));
   // real blocks
   const size_t nb = (size_t)n * L;
   AL(ctx->V, nb); AL(ctx->AV, nb); AL(ctx->BV, nb);

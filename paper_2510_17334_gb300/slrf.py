@@ -32,7 +32,7 @@ SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_app
            "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
            "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static", "slrf_setup_batched",
-           "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm")
+           "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm", "slrf_wait_selftest")
 
 
 class SlrfError(RuntimeError):
@@ -98,6 +98,7 @@ def lib() -> ct.CDLL:
         L.slrf_strerror.argtypes = [i]
         L.slrf_strerror.restype = ct.c_char_p
         L.slrf_last_error.argtypes = [vp]
+        L.slrf_wait_selftest.argtypes = [i, vp]
         _lib = L
     return _lib
 
@@ -401,6 +402,89 @@ def slrf_solve_host(rowptr, col, valA, valB, gamma, block_L, opts=None, V0=None,
     _check(rc, "slrf_solve_host")
     c = min(nf.value, cap)
     return ev[:c], X[:, :c], rs[:c], st.as_dict()
+
+
+def quadrature_table(rule: str, m: int, gamma: float):
+    """Pole table (upper-half poles sigma_j, weights w_j) of a classical contour-integral
+    filter, for slrf_opts_default(poles=..., weights=...): a quadrature rule for the Cauchy
+    integral of the interval's indicator over the circle through 0 and gamma (centre and
+    radius gamma/2), on the upper half circle theta in [0, pi]; the lower half is the
+    conjugate.  Rules (the comparison filters of the paper's Table 1):
+      "midpoint"        theta_j = pi (j - 1/2) / m, equal weights;
+      "gauss_legendre"  theta_j = pi (1 + x_j) / 2 at the Gauss-Legendre points x_j;
+      "gauss_chebyshev" x_j = cos((2j - 1) pi / (2m)), weights pi/m sqrt(1 - x_j^2).
+    The weight of node z_j = c + r e^{i theta_j} is -r e^{i theta_j} times its quadrature
+    weight on theta / (2 pi) (dz = i r e^{i theta} dtheta, and the factor -1/(2 pi i))."""
+    c = r = 0.5 * float(gamma)
+    j = np.arange(1, m + 1)
+    if rule == "midpoint":
+        theta = np.pi * (j - 0.5) / m
+        wq = np.full(m, np.pi / m)
+    elif rule == "gauss_legendre":
+        x, wx = np.polynomial.legendre.leggauss(m)
+        theta = np.pi * (1.0 + x) / 2.0
+        wq = wx * np.pi / 2.0
+    elif rule == "gauss_chebyshev":
+        x = np.cos((2 * j - 1) * np.pi / (2 * m))
+        theta = np.pi * (1.0 + x) / 2.0
+        wq = (np.pi / m) * np.sqrt(1.0 - x * x) * np.pi / 2.0
+    else:
+        raise ValueError(f"unknown rule {rule}")
+    z = np.exp(1j * theta)
+    return c + r * z, -r * z * wq / (2.0 * np.pi)
+
+
+def pole_shard(m: int, world: int, rank: int) -> list:
+    """Poles of rank `rank` when the m upper-half poles of a filter are split over `world`
+    ranks (round robin: j = rank, rank + world, ...).  Every pole belongs to exactly one rank."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank outside the world")
+    return list(range(rank, m, world))
+
+
+class ShardedFilter:
+    """Pole-sharded filter apply (the paper's first parallel level, Sec. 2.3): each rank
+    solves the shifted systems of its own poles and one sum all-reduce of the partial
+    blocks gives U = sum_j 2 Re(w_j Y_j) on every rank.  The warm start splits by pole as
+    well (Y_j = x/(theta - sigma_j) + correction), so a context built on a subset of the
+    pole table returns exactly that subset's share, including its part of Phi(theta) x.
+    The all-reduce is torch.distributed's (NCCL between GPUs); no kernel of the library
+    touches a peer's memory.  Ranks with no pole contribute zeros."""
+
+    def __init__(self, rowptr, col, valA, valB, gamma, block_L, opts, sigma, w, group=None, stream=None):
+        import torch.distributed as dist
+
+        self.dist = dist
+        self.group = group
+        world = dist.get_world_size(group)
+        rank = dist.get_rank(group)
+        mine = pole_shard(len(sigma), world, rank)
+        self.ctx = None
+        if mine:
+            sig = np.asarray(sigma)[mine]
+            ww = np.asarray(w)[mine]
+            o = Opts()
+            ct.memmove(ct.byref(o), ct.byref(opts), ct.sizeof(Opts))
+            arr_s = np.ascontiguousarray(np.stack([sig.real, sig.imag], axis=1).ravel())
+            arr_w = np.ascontiguousarray(np.stack([ww.real, ww.imag], axis=1).ravel())
+            o.m = len(mine)
+            o.poles = arr_s.ctypes.data
+            o.weights = arr_w.ctypes.data
+            o._keep = [arr_s, arr_w]
+            self.ctx = Context(rowptr, col, valA, valB, gamma, block_L, o, stream=stream)
+
+    def filter_apply(self, X: torch.Tensor, theta: torch.Tensor | None = None) -> torch.Tensor:
+        if self.ctx is not None:
+            U = self.ctx.filter_apply(X, theta)
+        else:
+            U = torch.zeros_like(_dev(X, torch.float64))
+        self.dist.all_reduce(U, op=self.dist.ReduceOp.SUM, group=self.group)
+        return U
+
+    def close(self):
+        if self.ctx is not None:
+            self.ctx.close()
+            self.ctx = None
 
 
 class SlrfEigsh(torch.autograd.Function):

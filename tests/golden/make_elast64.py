@@ -1,7 +1,10 @@
-"""Writes tests/golden/elast_64_spectrum.json: the reference spectrum of the 64 x 64 x 32 Q1
-elasticity box (z = 0 clamped, E lognormal(0, 0.5) seed 3) and the count of eigenvalues in
-(0, gamma] -- from oracle/ only (shift-invert Lanczos and a Sylvester-inertia count).  Takes
-about an hour and ~25 GB of host memory.
+"""Writes the reference values of the 64 x 64 x 32 Q1 elasticity box (z = 0 clamped, E
+lognormal(0, 0.5) seed 3) from oracle/ only:
+  spectrum -> tests/golden/elast_64_spectrum.json: the 330 lowest eigenvalues by
+              shift-invert Lanczos;
+  inertia  -> tests/golden/elast_64_count.json: the number of eigenvalues below gamma by
+              Sylvester's law of inertia (a symmetric sparse LU of A - gamma B).
+Each takes up to about an hour and ~25 GB of host memory.
 
     python tests/golden/make_elast64.py [spectrum|inertia]
 """
@@ -15,14 +18,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import slrf_oracle as orc  # noqa: E402
 from slrf_inputs import elastic as se  # noqa: E402
 
-OUT = os.path.join(HERE, "elast_64_spectrum.json")
-
-
 def main(what):
+    out = os.path.join(HERE, "elast_64_spectrum.json" if what == "spectrum" else "elast_64_count.json")
     tab = {}
-    if os.path.exists(OUT):
-        with open(OUT) as fh:
-            tab = json.load(fh)
     p = se.pencil("elast_64")
     A, B = p.A(), p.B()
     if what == "spectrum":
@@ -38,7 +36,7 @@ def main(what):
         tab["source_inertia"] = "oracle.inertia_count (SuperLU, symmetric mode, diagonal pivots) of A - gamma B"
     tab["n"] = p.n
     tab["nnz"] = p.nnz
-    with open(OUT, "w") as fh:
+    with open(out, "w") as fh:
         json.dump(tab, fh, indent=1)
     print({k: (v if not isinstance(v, list) else len(v)) for k, v in tab.items()})
 

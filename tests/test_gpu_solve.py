@@ -302,3 +302,27 @@ def test_adaptive_it_max_resolves_short_inner_solves(slrf_mod):
     assert rc == 0 and nf == cnt
     assert np.max(np.abs(ev - lam[:cnt]) / lam[:cnt]) <= 1e-10
     assert rs.max() <= 1e-8
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_bounded_waits_report_a_timeout_and_leave_the_device_usable(slrf_mod, kind):
+    """Failure detection without a fault: a wait that nothing can complete (kind 0: the
+    Rayleigh-Ritz grid barrier expecting one block more than the launch has; kind 1: an
+    mbarrier phase nobody arrives at) gives up at its limit and the call returns
+    SLRF_ETIMEOUT; a filter apply afterwards still runs and matches the oracle."""
+    import time
+
+    t0 = time.time()
+    assert slrf_mod.lib().slrf_wait_selftest(kind, None) == slrf_mod.SLRF_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    assert slrf_mod.lib().slrf_wait_selftest(2, None) == slrf_mod.SLRF_EINVAL
+    p = si.bar1d_pencil(300)
+    lam = pins.bar1d_eigs(300)
+    gamma = 0.5 * (lam[5] + lam[6])
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, 8, slrf_mod.slrf_opts_default(it_max=40))
+    V1 = si.start_block(300, 8, 2)
+    U = ctx.filter_apply(torch.from_numpy(V1)).cpu().numpy()
+    ctx.close()
+    so, wo = orc.slrf_poles(8, gamma)
+    Uo, _ = orc.filter_apply(p.A(), p.B(), V1, None, so, wo, 40, 1e-10)
+    assert rel(U, Uo) <= 1e-8

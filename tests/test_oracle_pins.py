@@ -490,3 +490,38 @@ def test_full_size_reference_routines_on_a_reduced_box():
     r = orc.enhanced_slrf(A, B, gamma, si.start_block(p.n, 30, 3), m=8, it_max=30, outer_max=60, precond=True)
     assert r.status == orc.OK and len(r.evals) == cnt
     assert np.max(np.abs(r.evals - lam[:cnt]) / lam[:cnt]) <= 1e-9
+
+
+def test_midpoint_quadrature_filter_is_the_butterworth_function():
+    """The trapezoidal (midpoint) rule on the circle through 0 and gamma gives exactly the
+    rational function 1 / (1 + ((t - c)/r)^(2m)), c = r = gamma/2: its 2m poles are the
+    roots of z^(2m) = -1 and its residues -z_k/(2m) (partial fractions)."""
+    g = 250.0
+    for m in (4, 8, 16):
+        s, w = orc.quadrature_poles("midpoint", m, g)
+        assert np.allclose(np.abs(s - g / 2), g / 2) and np.all(s.imag > 0)
+        t = np.linspace(-0.5, 2.5, 301) * g
+        ref = 1.0 / (1.0 + ((t - g / 2) / (g / 2)) ** (2 * m))
+        assert np.abs(orc.filter_value(t, s, w) - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("rule", ["gauss_legendre", "gauss_chebyshev"])
+def test_gauss_quadrature_filters_tend_to_the_indicator(rule):
+    """Gauss-Legendre and Gauss-Chebyshev rules on the half circle: the filter is 1 at the
+    centre (the weights integrate dtheta over [0, pi]: exactly for Legendre, to the rule's
+    error for Chebyshev), and Phi(t) -> 1 inside / 0 outside as m grows."""
+    g = 1.0
+    s, w = orc.quadrature_poles(rule, 8, g)
+    x, om = np.polynomial.legendre.leggauss(8)
+    if rule == "gauss_legendre":
+        assert abs(orc.filter_value(0.5 * g, s, w) - 1.0) <= 1e-13
+        assert np.allclose(np.sort(s.real), np.sort(0.5 * g + 0.5 * g * np.cos(np.pi * (1 + x) / 2)))
+    else:
+        assert abs(orc.filter_value(0.5 * g, s, w) - 1.0) <= 2e-2
+    errs = []
+    for m in (8, 32, 128):
+        s, w = orc.quadrature_poles(rule, m, g)
+        t_in = np.linspace(0.2, 0.8, 61)
+        t_out = np.concatenate([np.linspace(-1.0, -0.2, 41), np.linspace(1.2, 3.0, 41)])
+        errs.append(max(np.abs(orc.filter_value(t_in, s, w) - 1).max(), np.abs(orc.filter_value(t_out, s, w)).max()))
+    assert errs[2] < errs[1] < errs[0] and errs[2] <= 1e-3
