@@ -76,6 +76,37 @@ def slrf_poles(m: int, gamma: float, alpha: float = 1.0, beta: float = 0.01, ban
     return gamma * sig_hat, gamma * w_hat
 
 
+def quadrature_poles(rule: str, m: int, gamma: float):
+    """Upper-half poles and weights of the classical contour-integral filters the paper
+    compares with (Sec. 1, Table 1): the indicator of the interval written as the Cauchy
+    integral -(1/2 pi i) int dz/(t - z) over the circle z = c + r e^{i theta} through 0 and
+    gamma (c = r = gamma/2), with a quadrature rule on the upper half theta in [0, pi]; the
+    lower half is the conjugate, so Phi(t) = sum_j 2 Re(w_j/(t - sigma_j)) as for SLRF.
+      midpoint:        theta_j = pi (j - 1/2)/m,            w_j = -r e^{i theta_j} / (2m)
+      gauss_legendre:  theta_j = pi (1 + x_j)/2, x_j, omega_j the Gauss-Legendre rule on
+                       [-1, 1],                               w_j = -r e^{i theta_j} omega_j / 4
+      gauss_chebyshev: x_j = cos((2j - 1) pi/(2m)), omega_j = (pi/m) sqrt(1 - x_j^2) (the
+                       Chebyshev rule applied to int f(x) dx), theta_j as above,
+                                                              w_j = -r e^{i theta_j} omega_j / 4
+    """
+    c = r = 0.5 * gamma
+    j = np.arange(1, m + 1)
+    if rule == "midpoint":
+        th = np.pi * (j - 0.5) / m
+        om = np.full(m, 2.0 / m)  # so that w = -r e^{i theta} om / 4 = -r e^{i theta}/(2m)
+    elif rule == "gauss_legendre":
+        x, om = np.polynomial.legendre.leggauss(m)
+        th = np.pi * (1.0 + x) / 2.0
+    elif rule == "gauss_chebyshev":
+        x = np.cos((2 * j - 1) * np.pi / (2 * m))
+        om = (np.pi / m) * np.sqrt(1.0 - x * x)
+        th = np.pi * (1.0 + x) / 2.0
+    else:
+        raise ValueError(rule)
+    e = np.exp(1j * th)
+    return c + r * e, -r * e * om / 4.0
+
+
 def filter_value(t, sigma, w):
     """Phi(t) for real t with the conjugate half implied: sum_j 2 Re(w_j / (t - sigma_j))."""
     t = np.asarray(t, dtype=np.float64)

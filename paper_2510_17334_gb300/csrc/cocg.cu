@@ -214,7 +214,7 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
       R gv = 0, agv = 0, bgv = 0;
       if (ok[v]) {
         const size_t o = (size_t)i * a.ldg + cidx[v];
-        gv = (R)a.g[o]; agv = (R)a.Ag[o]; bgv = (R)a.Bg[o];
+        if (CHK(1, o, (long long)a.n * a.ldg)) { gv = (R)a.g[o]; agv = (R)a.Ag[o]; bgv = (R)a.Bg[o]; }
       }
       C r0; r0.x = cf[v].x * gv; r0.y = cf[v].y * gv;
       C t; t.x = agv - sg[v].x * bgv; t.y = -sg[v].y * bgv;
@@ -227,9 +227,11 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
       acc[v][4] += r0.x * r0.x + r0.y * r0.y;
     }
     const size_t off = (size_t)i * a.W + w0;
-    stv<R>(a.r + off, rv);
-    stv<R>(a.p + off, rv);
-    stv<R>(a.q + off, qv);
+    if (CHK(2, off + VEC - 1, (long long)a.n * a.W)) {
+      stv<R>(a.r + off, rv);
+      stv<R>(a.p + off, rv);
+      stv<R>(a.q + off, qv);
+    }
   }
   double out[NQ];
   int w;
@@ -300,6 +302,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
   const int lanes_per_col = a.mp >= VEC ? a.mp / VEC : 1;
   const bool warp_act = __any_sync(0xffffffffu, any_act);
   const int cpt = 32 * VEC / a.mp;  // columns of a tile (kAccU accumulator layout)
+#pragma unroll 1
   for (int64_t i = i0 + warp; i < i1; i += kWarps) {
     const size_t off = (size_t)i * a.W + w0;
     Vec<R> dv;
@@ -323,11 +326,16 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
 #pragma unroll
         for (int v = 0; v < VEC; ++v) dv.z[v] = cmake<C>(0, 0);
       } else if (any_act || FINAL) {
-        dv = ldv<R>(a.d + off);
+        if (CHK(3, off + VEC - 1, (long long)a.n * a.W)) dv = ldv<R>(a.d + off);
       }
     }
     if (any_act) {
-      Vec<R> pv = ldv<R>(a.p + off), qv = ldv<R>(a.q + off), rv = ldv<R>(a.r + off);
+      Vec<R> pv, qv, rv;
+      if (CHK(4, off + VEC - 1, (long long)a.n * a.W)) {
+        pv = ldv<R>(a.p + off);
+        qv = ldv<R>(a.q + off);
+        rv = ldv<R>(a.r + off);
+      }
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         if (act[v]) {
@@ -344,7 +352,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         acc[v][1] += 2 * rr.x * rr.y;
         acc[v][2] += rr.x * rr.x + rr.y * rr.y;
       }
-      stv<R>(a.r + off, rv);
+      if (CHK(5, off + VEC - 1, (long long)a.n * a.W)) stv<R>(a.r + off, rv);
     }
     if constexpr (ACCU) {
       if (FIRST || ACCU_END || warp_act) {
@@ -376,7 +384,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
       }
       continue;
     }
-    if (FIRST || any_act) stv<R>(a.d + off, dv);
+    if ((FIRST || any_act) && CHK(6, off + VEC - 1, (long long)a.n * a.W)) stv<R>(a.d + off, dv);
     if (FM == kFinalStoreD || FM == kFinalAddD) {
       // refinement: accumulate this step's correction into the FP64 D
 #pragma unroll
@@ -410,7 +418,8 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         if ((lane % lanes_per_col) == 0 && c < a.k) {
           if (a.gscale != nullptr) s /= a.gscale[c];
           if (a.dsc != nullptr) s *= ds;
-          a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
+          if (CHK(7, (long long)i * a.ldu + c, (long long)a.n * a.ldu) && CHK(8, c, a.k))
+            a.U[(size_t)i * a.ldu + c] = a.coefV[c] * a.V[(size_t)i * a.ldv + c] + s;
         }
       } else {
 #pragma unroll
@@ -680,10 +689,14 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
       const int64_t c = a.gptr[g + 1] - a.gptr[g];
       return c <= 0 ? 1 : (int)((c + CH - 1) / CH);
     };
+    const int64_t nrec = a.gptr[a.ngroups];  // records in all (bounds of every copy)
     auto first = [&](int64_t g, int c, int &cnt) -> int64_t {
       const int64_t e0 = a.gptr[g] + (int64_t)c * CH, e1 = a.gptr[g + 1];
       cnt = (int)(e1 - e0 < CH ? e1 - e0 : CH);
-      if (cnt < 0) cnt = 0;
+      if (cnt < 0 || e0 < 0 || e0 + cnt > nrec) {
+        if (cnt != 0) atomicCAS(a.err, 0, 2);  // inconsistent offsets: copy nothing
+        cnt = 0;
+      }
       return e0;
     };
     auto issue = [&](int b, int64_t g, int c) {
@@ -727,7 +740,12 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
 #pragma unroll kGrpUnroll
       for (int t = 0; t < cnt; ++t) {
         const unsigned char *rp = rb_ + t * RS;
-        const int c = *reinterpret_cast<const int *>(rp + 16 * G);
+        int c = *reinterpret_cast<const int *>(rp + 16 * G);
+        if ((unsigned)c >= (unsigned)a.n) {  // a corrupt record: flag it, gather row 0
+          atomicCAS(a.err, 0, 3);
+          (void)CHK(21, c, a.n);
+          c = 0;
+        }
         const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
         // the record's 2 G values in G 16-byte broadcast loads
         float4 rv4[G];
@@ -768,6 +786,7 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
           const int64_t i = cg * G + j;
           if (i < a.n) {
             const size_t off = (size_t)i * a.W + w0;
+            if (!CHK(20, off + VEC - 1, (long long)a.n * a.W)) continue;
             const Vec<R> rv = ldv<R>(a.r + off);
             Vec<R> pv, qv;
             if (!FRESH) {
@@ -1163,8 +1182,16 @@ template <typename R> static dim3 grid_of(const CocgArgs<R> &a) {
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
   cocg_init_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
 }
+// A mode whose buffers are missing launches nothing: code 4 in *a.err (status SLRF_EINVAL)
+template <typename R> static bool mode_guard(const CocgArgs<R> &a, int fm, cudaStream_t st) {
+  if (cocg_mode_ok(a, fm)) return true;
+  // low byte only (a memset is allowed under stream capture); the flag starts at zero
+  if (a.err != nullptr) cudaMemsetAsync(a.err, 4, 1, st);
+  return false;
+}
 template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st, int tile0,
                                       int ntiles) {
+  if (!mode_guard(a, fm, st)) return;
   dim3 g = grid_of(a);
   if (ntiles > 0) g.y = (unsigned)ntiles;
 #define UPD(F, M) cocg_update_kernel<R, F, M><<<g, kThreads, 0, st>>>(a, tile0)
@@ -1193,6 +1220,7 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
 }
 template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
                                     cudaStream_t st) {
+  if (!mode_guard(a, fm, st)) return;
   const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
 #define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
   if (first) {

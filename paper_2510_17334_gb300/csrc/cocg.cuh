@@ -74,7 +74,8 @@ struct CocgArgs {
   int64_t ngroups;
   const int64_t *gptr;       // [ngroups + 1]
   const unsigned char *grec; // records, 16-byte aligned
-  int *err;                  // set to 1 when a bounded wait gives up (SLRF_ETIMEOUT)
+  int *err;                  // 1: a bounded wait gave up (SLRF_ETIMEOUT); 2, 3: group records
+                             // inconsistent; 4: update buffers missing (SLRF_EINVAL)
   // Jacobi preconditioner D = diag(A): the value arrays above are those of
   // D^-1/2 A D^-1/2 and D^-1/2 B D^-1/2, g is D^-1/2 g, and dsc[i] = D_ii^-1/2 turns the
   // scaled solutions back (y = D^-1/2 z) in the pole sum; null: no preconditioner
@@ -98,6 +99,19 @@ template <int G> __host__ __device__ constexpr int grp_smem_bytes() { return kWa
 enum FinalMode {
   kFinalNone = 0, kFinalU = 1, kFinalStoreD = 2, kFinalAddD = 3, kFinalUFromD = 4, kAccU = 5, kAccUEnd = 6
 };
+// Whether the buffers an update in mode `fm` writes or reads are present (the refinement
+// modes need D64, the accumulator modes uacc, the modes that write U need U, V, coefV).
+// The launchers skip a launch that fails this and record code 4 in *a.err.
+template <typename R> inline bool cocg_mode_ok(const CocgArgs<R> &a, int fm) {
+  const bool needs_d64 = fm == kFinalStoreD || fm == kFinalAddD || fm == kFinalUFromD;
+  const bool needs_acc = fm == kAccU || fm == kAccUEnd;
+  const bool writes_u = fm == kFinalU || fm == kFinalUFromD || fm == kAccUEnd;
+  if (fm < kFinalNone || fm > kAccUEnd) return false;
+  if (needs_d64 && a.D64 == nullptr) return false;
+  if (needs_acc && a.uacc == nullptr) return false;
+  if (writes_u && (a.U == nullptr || a.V == nullptr || a.coefV == nullptr)) return false;
+  return true;
+}
 
 // Launchers (defined in cocg.cu).  All enqueue on `st`.
 template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 namespace slrf {
 
@@ -58,6 +59,26 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
         "l"(*reinterpret_cast<unsigned long long *>(&c)));
   return *reinterpret_cast<float2 *>(&d);
 }
+
+// ---------------------------------------------------------------- debug bounds checks
+// SLRF_CHECKS=1 (a debug build): every checked global access verifies its index against
+// the extent the kernel was given; the first violation is printed with its site, the
+// access is skipped.  Off by default (CHK is then the constant true).
+#ifndef SLRF_CHECKS
+#define SLRF_CHECKS 0
+#endif
+#if SLRF_CHECKS
+__device__ __noinline__ inline bool slrf_chk_fail(int site, long long idx, long long bound) {
+  printf("SLRF_CHECK site %d idx %lld bound %lld block (%d,%d) thread %d\n", site, idx, bound, (int)blockIdx.x,
+         (int)blockIdx.y, (int)threadIdx.x);
+  return false;
+}
+#define CHK(site, idx, bound)                                                    \
+  ((((long long)(idx)) >= 0 && ((long long)(idx)) < ((long long)(bound))) || \
+   slrf_chk_fail((site), (long long)(idx), (long long)(bound)))
+#else
+#define CHK(site, idx, bound) true
+#endif
 
 // ---------------------------------------------------------------- reductions
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {

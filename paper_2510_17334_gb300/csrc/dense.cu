@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
       const double *xr = reinterpret_cast<const double *>(xl + (unsigned long long)(unsigned)c * row_bytes);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (c0 + 32 * u < k) {
+        if (c0 + 32 * u < k && CHK(40, (long long)c * ldx + c0 + 32 * u, (long long)n * ldx)) {
           const double x = xr[32 * u];
           if (YA) sa[u] = fma(ab.x, x, sa[u]);
           if (YB) sb[u] = fma(ab.y, x, sb[u]);
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) spmm_real_kernel(int64_t n, const int64_t
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int cc = c0 + 32 * u;
-    if (cc < k) {
+    if (cc < k && CHK(41, (long long)i * ldy + cc, (long long)n * ldy)) {
       if (YA) YA[(size_t)i * ldy + cc] = sa[u];
       if (YB) YB[(size_t)i * ldy + cc] = sb[u];
     }
@@ -275,7 +275,7 @@ __global__ void row_scale_kernel(int64_t n, int k, const double *__restrict__ s,
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;
   const int64_t i = t / k;
-  X[i * ldx + t % k] *= s[i];
+  if (CHK(42, i * ldx + t % k, n * ldx)) X[i * ldx + t % k] *= s[i];
 }
 void row_scale(int64_t n, int k, const double *s, double *X, int ldx, cudaStream_t st) {
   const int64_t tot = n * k;

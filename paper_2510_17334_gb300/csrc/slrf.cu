@@ -7,6 +7,7 @@
 // The host drives the outer loop; the only device->host transfer per outer iteration is
 // a handful of integers for the lock decision (the locking step of Alg. 2).
 #include <cuda_runtime.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -373,6 +374,19 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   return a;
 }
 
+// Update modes of refinement step `step` of `nref`: the middle updates and the last one.
+// FP32 without refinement: every update adds its step to the accumulator (kAccU, no d
+// array); in FP64 the extra complex product per entry costs more on the FP64 pipe than the
+// d traffic it saves, so the FP64 path keeps d and its last update writes U (kFinalU).
+template <typename R> static void update_modes(int nref, int step, int &fm_mid, int &fm_last) {
+  const bool accu = nref == 1 && sizeof(R) == 4;
+  fm_mid = accu ? kAccU : kFinalNone;
+  fm_last = accu        ? kAccUEnd
+            : nref == 1 ? kFinalU
+            : step == 1 ? kFinalStoreD
+                        : (step < nref ? kFinalAddD : kFinalUFromD);
+}
+
 template <typename R>
 static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double *theta, double *U, int ldu,
                     bool capture_ok, FilterTiming *tm) {
@@ -401,13 +415,8 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
         if constexpr (sizeof(R) == 4) launch(0, [&] { cocg_residual<R>(a, s); });
         launch(1, [&] { cocg_spmm<R>(a, s, true); });
       }
-      // FP32 without refinement: every update adds its step to the accumulator (kAccU, no d
-      // array); in FP64 the extra complex product per entry costs more on the FP64 pipe than
-      // the d traffic it saves, so the FP64 path keeps d
-      const bool accu = nref == 1 && sizeof(R) == 4;
-      const int fm_mid = accu ? kAccU : kFinalNone;
-      const int fm_last = accu ? kAccUEnd
-                               : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+      int fm_mid, fm_last;
+      update_modes<R>(nref, step, fm_mid, fm_last);
       if (dual && dual_ok) {
         const int n0 = T / 2, n1 = T - n0;  // group 0: tiles [0, n0), group 1: [n0, T)
         launch(2, [&] { cocg_update<R>(a, true, fm_mid, s, 0, n0); });  // U_1 of group 0
@@ -437,6 +446,12 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
       cudaEventRecord(e0, s);
       fn();
       cudaEventRecord(e1, s);
+#if SLRF_CHECKS
+      {  // debug build: run launch by launch and report the first one that fails
+        const cudaError_t e = cudaStreamSynchronize(s);
+        fprintf(stderr, "slrf timed launch %zu kind %d: %s\n", evs.size(), kind, cudaGetErrorString(e));
+      }
+#endif
       evs.push_back({kind, {e0, e1}});
     };
     body(s, timed, false);
@@ -739,11 +754,8 @@ static void batch_cocg(slrf_batch *b, int P, int total, int nref, int itm, cudaS
       if constexpr (sizeof(R) == 4) cocg_residual_batched_launch<R>(args, pre, P, total, s);
       cocg_spmm_batched_launch<R>(args, pre, P, total, true, s);
     }
-    // as in the single-problem schedule: FP32 without refinement accumulates every update's step
-    const bool accu = nref == 1 && sizeof(R) == 4;
-    const int fm_mid = accu ? kAccU : kFinalNone;
-    const int fm_last = accu ? kAccUEnd
-                             : nref == 1 ? kFinalU : (step == 1 ? kFinalStoreD : (step < nref ? kFinalAddD : kFinalUFromD));
+    int fm_mid, fm_last;
+    update_modes<R>(nref, step, fm_mid, fm_last);
     for (int it = 1; it <= itm; ++it) {
       cocg_update_batched_launch<R>(args, pre, P, total, it == 1, it == itm ? fm_last : fm_mid, s);
       if (it < itm) cocg_spmm_batched_launch<R>(args, pre, P, total, false, s);
@@ -768,6 +780,11 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
     if (rc != SLRF_OK) return rc;
     ha[i] = build_cocg_args<R>(c, c->V, c->L, k, c->U, c->L, nref);
     ha[i].it_cap = c->o.it_adapt ? c->it_cur : 0;  // per-problem It_max inside the shared loop
+    for (int step = 1; step <= nref; ++step) {  // the batched kernels read these buffers unchecked
+      int fm_mid, fm_last;
+      update_modes<R>(nref, step, fm_mid, fm_last);
+      if (!cocg_mode_ok(ha[i], fm_mid) || !cocg_mode_ok(ha[i], fm_last)) return SLRF_EINVAL;
+    }
     itm = std::max(itm, c->it_cur > 0 ? c->it_cur : c->o.it_max);
     cocg_prepare(ha[i].W, k, c->m, c->mp, c->sig, c->wt, th, c->cfac, c->coefV, c->ws, c->st);
     if (sizeof(R) == 4) col_scale(c->n, k, c->G, c->L, c->gmax, c->gscale, c->st);
@@ -1308,7 +1325,9 @@ int slrf_solve(slrf_ctx *ctx, const double *V0, int cap, int *n_found, double *e
       ms_d += b;
     }
     const int *hf = ctx->h_iflags;
-    if (hf[9] != 0 || hf[13] != 0 || hf[15] != 0) { status = SLRF_ETIMEOUT; break; }
+    // hf[15]: 1 a bounded wait gave up; 2-4 inconsistent group records or update buffers
+    if (hf[9] != 0 || hf[13] != 0 || hf[15] == 1) { status = SLRF_ETIMEOUT; break; }
+    if (hf[15] != 0) { status = SLRF_EINVAL; break; }
     if (hf[4] != 0) { status = SLRF_ECHOL; break; }
     nconv = hf[0];
     k = hf[1];
@@ -1520,7 +1539,8 @@ int slrf_solve_batched(slrf_batch *b, const double *const *V0, const int *caps, 
       CK(cudaStreamSynchronize(c->st));
       const int *hf = c->h_iflags;
       outer_of[p] = outer;
-      if (hf[9] != 0 || hf[13] != 0) { st_p[p] = SLRF_ETIMEOUT; done[p] = 1; continue; }
+      if (hf[9] != 0 || hf[13] != 0 || hf[15] == 1) { st_p[p] = SLRF_ETIMEOUT; done[p] = 1; continue; }
+      if (hf[15] != 0) { st_p[p] = SLRF_EINVAL; done[p] = 1; continue; }
       if (hf[4] != 0) { st_p[p] = SLRF_ECHOL; done[p] = 1; continue; }
       nconv[p] = hf[0];
       kk[p] = hf[1];
