@@ -3,8 +3,12 @@
 One step = one slrf_solve of the workload: every outer iteration's filter apply (all
 poles x columns by COCG), B-orthogonalisation against the locked vectors, Cholesky-QR2,
 Rayleigh-Ritz, residuals, locking and the warm start.  Default workload: the 3D Q1
-Laplacian on 41^3 nodes (n = 68,921, 27 nnz/row), gamma = 259.0666 (105 eigenpairs),
-block 160, m = 8 poles, FP64.
+linear-elasticity box of 64 x 64 x 32 elements (65 x 65 x 33 nodes, z = 0 face clamped,
+n = 380,928, 29.6M stored entries, lognormal Young's modulus), gamma = 220.8176 (305
+eigenpairs below it), block 480, m = 8 poles, Jacobi-preconditioned inner solves, complex-FP32
+COCG in FP64 refinement (It_max 30); the same solve in FP64 is the "compare" record.  Other
+workloads (--workload): q1_lap_41 (3D Q1 Laplacian on 41^3 nodes), elast_32 / elast_48,
+bar1d_2000, batch64 (64 uneven pencils solved together), sens48 (48 scaled pencils).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -364,6 +368,8 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes of one SpMM launch from an ncu capture of this build (else null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--counts-out", default=None,
+                    help="write the timed solve's counts (the reference arm's scaling) to this JSON file")
     ap.add_argument("--no-tables", action="store_true",
                     help="skip the small-problem records of the paper's Tables 1 and 3")
     ap.add_argument("--clocks-csv", default=None,
@@ -519,6 +525,12 @@ def main():
         line["cpu_baseline"] = cpu_baseline_subprocess(args.workload, it_main, precond, nf,
                                                        int(col_iters / args.steps), st["outer_iters"],
                                                        int(col_solves / args.steps), wl.m)
+    if rank == 0 and args.counts_out:
+        rec = {"it_max": it_main, "precond": precond, "precision": prec, "n_found": nf,
+               "column_iterations": int(col_iters / args.steps), "outer": st["outer_iters"],
+               "column_solves": int(col_solves / args.steps)}
+        with open(args.counts_out, "w") as fh:
+            json.dump({args.workload: rec}, fh, indent=1)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

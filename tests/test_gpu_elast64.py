@@ -33,19 +33,25 @@ def box():
     gamma, _ = se.gamma("elast_64")
     with open(os.path.join(GOLD, "elast_64_spectrum.json")) as fh:
         lam = np.array(json.load(fh)["lambdas"])
+    return p, gamma, lam
+
+
+@pytest.fixture(scope="module")
+def count(box):
+    _, gamma, _ = box
     with open(os.path.join(GOLD, "elast_64_count.json")) as fh:
         cnt = json.load(fh)
     assert cnt["inertia_symmetric_ordering"] and abs(cnt["gamma"] - gamma) == 0.0
-    return p, gamma, lam, cnt["inertia_count"]
+    return cnt["inertia_count"]
 
 
-def test_reference_count_agrees_with_the_reference_spectrum(box):
-    p, gamma, lam, count = box
+def test_reference_count_agrees_with_the_reference_spectrum(box, count):
+    p, gamma, lam = box
     assert count == int(np.sum(lam <= gamma))
 
 
-def test_mixed_solve_at_the_benched_settings(slrf_mod, box):
-    p, gamma, lam, count = box
+def test_mixed_solve_at_the_benched_settings(slrf_mod, box, count):
+    p, gamma, lam = box
     L = se.SPECS["elast_64"]["block"]
     opts = slrf_mod.slrf_opts_default(it_max=30, precision=1, precond=1)
     ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, L, opts)
@@ -62,7 +68,7 @@ def test_mixed_solve_at_the_benched_settings(slrf_mod, box):
 
 
 def test_fp64_filter_full_width_sampled_columns(slrf_mod, box):
-    p, gamma, lam, count = box
+    p, gamma, lam = box
     L = se.SPECS["elast_64"]["block"]
     it = 4
     opts = slrf_mod.slrf_opts_default(it_max=it, precision=0, precond=1)
