@@ -672,10 +672,15 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
   R acc[VEC][2];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) acc[v][0] = acc[v][1] = R(0);
-  const int gpb = a.rows_per_block / G;  // groups per row block (rows_per_block is a multiple of G)
-  const int64_t gb0 = (int64_t)rb * gpb;
-  const int64_t gb1 = (gb0 + gpb < a.ngroups ? gb0 + gpb : a.ngroups);
-  if (warp_act && gb0 + warp < gb1) {
+  // Interleaved assignment: block rb takes the stripes rb, rb + nrb, rb + 2 nrb, ... of
+  // kWarps consecutive groups (one per warp).  The blocks in flight then sweep the matrix
+  // together through a window of about nrb stripes, so a gathered row of r is reused by all
+  // the groups that need it while it is still in L2, also when one column tile of r is
+  // larger than L2 (nrb is one resident wave of this kernel).
+  const int64_t gstride = (int64_t)a.nrb * kWarps;
+  const int64_t gb1 = a.ngroups;
+  const int64_t gfirst = (int64_t)rb * kWarps + warp;
+  if (warp_act && gfirst < gb1) {
     if (lane == 0) {
       mbar_init(bar, 1);
       mbar_init(bar + 1, 1);
@@ -684,7 +689,7 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
     __syncwarp();
     const char *const rlane = reinterpret_cast<const char *>(a.r + w0);
     const unsigned wbytes = (unsigned)a.W * (unsigned)sizeof(C);
-    // work items (group, chunk) of this warp: groups gb0 + warp, + kWarps, ...
+    // work items (group, chunk) of this warp: groups gfirst, + gstride, ...
     auto nchunks = [&](int64_t g) -> int {
       const int64_t c = a.gptr[g + 1] - a.gptr[g];
       return c <= 0 ? 1 : (int)((c + CH - 1) / CH);
@@ -714,11 +719,11 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
         }
       }
     };
-    int64_t cg = gb0 + warp, ng = cg;  // current item, next item
+    int64_t cg = gfirst, ng = cg;  // current item, next item
     int cc = 0, nc = 0;
     auto advance = [&](int64_t &g, int &c) {
       if (c + 1 < nchunks(g)) ++c;
-      else { g += kWarps; c = 0; }
+      else { g += gstride; c = 0; }
     };
     issue(0, cg, cc);
     advance(ng, nc);
@@ -1273,6 +1278,23 @@ void cocg_kernel_attrs() {
   grp_attrs<double, 4>();
   cudaGetLastError();
   done = true;
+}
+template <typename R, int G> static int grp_occ() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, G, false>, kThreads,
+                                                    grp_smem_bytes<G>()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
+}
+int grp_blocks_per_sm(int G, bool fp32) {
+  switch (G) {
+    case 2: return fp32 ? grp_occ<float, 2>() : grp_occ<double, 2>();
+    case 3: return fp32 ? grp_occ<float, 3>() : grp_occ<double, 3>();
+    case 4: return fp32 ? grp_occ<float, 4>() : grp_occ<double, 4>();
+    default: return 0;
+  }
 }
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st) {
   cocg_residual_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);

@@ -152,6 +152,8 @@ template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args,
 // Raise the dynamic shared-memory limit of the grouped SpMM kernels (once per process;
 // call before the first launch and outside stream capture).
 void cocg_kernel_attrs();
+// Resident blocks per SM of the grouped SpMM of height G (after cocg_kernel_attrs; 0 on error).
+int grp_blocks_per_sm(int G, bool fp32);
 
 
 // Grouped-row format: cnt[g] = number of distinct columns of rows [G g, G g + G) (grp_count),

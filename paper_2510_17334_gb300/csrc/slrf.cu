@@ -86,6 +86,7 @@ struct slrf_ctx {
   int last_k = 0, last_W = 0;
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
   int64_t rpb_tuned = 0;             // autotuned COCG rows per block (0 = default)
+  int grp_bpsm = 0;                  // resident blocks per SM of the grouped SpMM in use
   // real n x L blocks (ld = L)
   double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
   double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
@@ -249,6 +250,7 @@ static void drop_groups(slrf_ctx *ctx) {
   ctx->grec = nullptr;
   ctx->grp = 1;
   ctx->ngroups = 0;
+  ctx->grp_bpsm = 0;
 }
 static int build_groups(slrf_ctx *ctx, int G) {
   drop_groups(ctx);
@@ -271,6 +273,7 @@ static int build_groups(slrf_ctx *ctx, int G) {
   if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
   ctx->grp = G;
   ctx->ngroups = ng;
+  ctx->grp_bpsm = grp_blocks_per_sm(G, ctx->mixed);
   return SLRF_OK;
 }
 // Candidate G from the pattern.  FP64: the SpMM is bound by the FP64 pipe, so only groups
@@ -318,17 +321,24 @@ struct FilterTiming {
   int n_spmm = 0, n_update = 0;
 };
 
+// Row blocks per column tile before autotuning.  Plain CSR: about as many as the GPU
+// holds resident (SMs x 4 blocks), so that the blocks in flight at any time all belong to
+// one or two tiles (the tile index varies slowest) and the gathered rows of those tiles stay
+// in L2.  Grouped SpMM: exactly one resident wave of that kernel, whose blocks take
+// interleaved stripes of groups and so sweep the rows of a tile together.
+static int64_t row_blocks(const slrf_ctx *ctx) {
+  const int per_sm = (ctx->grp > 1 && ctx->grp_bpsm > 0) ? std::min(ctx->grp_bpsm, 4) : 4;
+  return (int64_t)ctx->sm_count * per_sm;
+}
+
 // COCG arguments of one filter apply of this context (k columns, optional warm start).
 template <typename R>
 static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int k, double *U, int ldu, int &nref) {
   const int vec = cocg_vec<R>();
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
-  // Row blocks per tile: about as many as the GPU holds resident (SMs x 4 blocks), so
-  // that the blocks in flight at any time all belong to one or two tiles (the tile index
-  // varies slowest) and the gathered rows of those tiles stay in L2.  An autotuned row
-  // count (slrf_opts.autotune) replaces the default.
-  const int64_t rblocks = (int64_t)ctx->sm_count * 4;
+  // row blocks per tile (row_blocks); an autotuned row count (slrf_opts.autotune) replaces it
+  const int64_t rblocks = row_blocks(ctx);
   int64_t rpb = std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
   if (ctx->rpb_tuned > 0) rpb = std::max<int64_t>(rpb, ctx->rpb_tuned);
   // whole groups per row block, the same number for every warp of the block
@@ -543,8 +553,10 @@ static int autotune_rows(slrf_ctx *ctx) {
   gaussian_block(ctx->n, L, ctx->o.seed + 7, ctx->V, L, st);
   int rc = filter_prep(ctx, ctx->V, L, L, nullptr, nullptr, nullptr);
   if (rc != SLRF_OK) return rc;
-  const int64_t rblocks = (int64_t)ctx->sm_count * 4;
-  const int64_t base = std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
+  auto base_rows = [&]() {
+    const int64_t rblocks = row_blocks(ctx);
+    return std::max<int64_t>(16, (ctx->n + rblocks - 1) / rblocks);
+  };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -587,6 +599,7 @@ static int autotune_rows(slrf_ctx *ctx) {
       return rc;
     }
   }
+  const int64_t base = base_rows();
   const int64_t cand[] = {base, 32, 64, 128, 256};
   best = 1e30f;
   int64_t best_r = 0;
