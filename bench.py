@@ -3,7 +3,7 @@
 One step = one slrf_solve of the workload: every outer iteration's filter apply (all
 poles x columns by COCG), B-orthogonalisation against the locked vectors, Cholesky-QR2,
 Rayleigh-Ritz, residuals, locking and the warm start.  Default workload: the 3D Q1
-linear-elasticity box of 64 x 64 x 32 elements (65 x 65 x 33 nodes, z = 0 face clamped,
+linear-elasticity box on 64 x 64 x 32 nodes (3 dof per node, the z = 0 layer clamped,
 n = 380,928, 29.6M stored entries, lognormal Young's modulus), gamma = 220.8176 (305
 eigenpairs below it), block 480, m = 8 poles, Jacobi-preconditioned inner solves, complex-FP32
 COCG in FP64 refinement (It_max 30); the same solve in FP64 is the "compare" record.  Other

@@ -150,6 +150,20 @@ int slrf_get_poles(slrf_ctx *ctx, int *m_out, double *sigma, double *w);
  * Errors: SLRF_EINVAL (k < 1 or k > L, NULL X or U), SLRF_ESTATE, SLRF_ECUDA. */
 int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U);
 
+/* Products with the context's matrices: AX = A X and BX = B X (either may be NULL, not
+ * both) for a real block X (device, n x k row-major, k <= L); AX and BX (device, n x k
+ * row-major) may alias neither X nor each other.  These are the products the outer
+ * iteration of Alg. 2 forms (the real sweep that starts the filter, the Gram matrices of
+ * the B-orthonormalisation and Rayleigh-Ritz, Sec. 4).  fp32 = 0: FP64 products and sums
+ * (the stored CSR values).  fp32 = 1: FP32 products and sums, through the grouped-row
+ * records of a precision = 1 context when it has them (G > 1; with precond = 1 those
+ * hold D^-1/2 A D^-1/2 and D^-1/2 B D^-1/2, and the result is scaled back by D^1/2 on both
+ * sides), else through the CSR values rounded to FP32.  Asynchronous on the context
+ * stream.
+ * Errors: SLRF_EINVAL (k < 1 or k > L, NULL X, both outputs NULL, aliasing), SLRF_ESTATE,
+ * SLRF_ECUDA. */
+int slrf_apply(slrf_ctx *ctx, const double *X, int k, double *AX, double *BX, int fp32);
+
 /* Measurement hook: the same computation and result as slrf_filter_apply, launched
  * kernel by kernel (no CUDA graph) with CUDA events around every COCG launch on the
  * library stream.  HOST outputs: ms[0] total device time of the call, ms[1] summed time

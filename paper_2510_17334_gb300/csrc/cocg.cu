@@ -23,6 +23,8 @@
 // them in a fixed order (deterministic) and updates the per-column scalars.
 #include "cocg.cuh"
 
+#include <type_traits>
+
 #ifndef SLRF_GATHER_UNROLL
 #define SLRF_GATHER_UNROLL 8
 #endif
@@ -48,17 +50,16 @@ constexpr int kGrpUnroll = SLRF_GRP_UNROLL;        // grouped records in flight 
 
 namespace slrf {
 
-template <typename R> struct Vec;
-template <> struct Vec<double> { double2 z[1]; };
-template <> struct Vec<float> { float2 z[SLRF_F32_VEC]; };
+// VEC complex entries of one lane (16-byte loads: one in FP64, VEC / 2 in FP32)
+template <typename R, int V> struct Vec { cx_t<R> z[V]; };
 
-template <typename R> __device__ __forceinline__ Vec<R> ldv(const cx_t<R> *p) {
-  Vec<R> v;
+template <typename R, int V> __device__ __forceinline__ Vec<R, V> ldv(const cx_t<R> *p) {
+  Vec<R, V> v;
   if constexpr (sizeof(R) == 8) {
     v.z[0] = *reinterpret_cast<const double2 *>(p);
   } else {
 #pragma unroll
-    for (int j = 0; j < SLRF_F32_VEC / 2; ++j) {
+    for (int j = 0; j < V / 2; ++j) {
       const float4 t = reinterpret_cast<const float4 *>(p)[j];
       v.z[2 * j] = make_float2(t.x, t.y);
       v.z[2 * j + 1] = make_float2(t.z, t.w);
@@ -66,12 +67,12 @@ template <typename R> __device__ __forceinline__ Vec<R> ldv(const cx_t<R> *p) {
   }
   return v;
 }
-template <typename R> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<R> &v) {
+template <typename R, int V> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<R, V> &v) {
   if constexpr (sizeof(R) == 8) {
     *reinterpret_cast<double2 *>(p) = v.z[0];
   } else {
 #pragma unroll
-    for (int j = 0; j < SLRF_F32_VEC / 2; ++j)
+    for (int j = 0; j < V / 2; ++j)
       reinterpret_cast<float4 *>(p)[j] = make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y);
   }
 }
@@ -81,16 +82,16 @@ template <typename R> __device__ __forceinline__ void stv(cx_t<R> *p, const Vec<
 #ifndef SLRF_SPMM_STREAM
 #define SLRF_SPMM_STREAM 1
 #endif
-template <typename R> __device__ __forceinline__ Vec<R> ldv_cs(const cx_t<R> *p) {
+template <typename R, int V> __device__ __forceinline__ Vec<R, V> ldv_cs(const cx_t<R> *p) {
   if constexpr (SLRF_SPMM_STREAM == 0) {
-    return ldv<R>(p);
+    return ldv<R, V>(p);
   } else {
-    Vec<R> v;
+    Vec<R, V> v;
     if constexpr (sizeof(R) == 8) {
       v.z[0] = __ldcs(reinterpret_cast<const double2 *>(p));
     } else {
 #pragma unroll
-      for (int j = 0; j < SLRF_F32_VEC / 2; ++j) {
+      for (int j = 0; j < V / 2; ++j) {
         const float4 t = __ldcs(reinterpret_cast<const float4 *>(p) + j);
         v.z[2 * j] = make_float2(t.x, t.y);
         v.z[2 * j + 1] = make_float2(t.z, t.w);
@@ -99,14 +100,14 @@ template <typename R> __device__ __forceinline__ Vec<R> ldv_cs(const cx_t<R> *p)
     return v;
   }
 }
-template <typename R> __device__ __forceinline__ void stv_cs(cx_t<R> *p, const Vec<R> &v) {
+template <typename R, int V> __device__ __forceinline__ void stv_cs(cx_t<R> *p, const Vec<R, V> &v) {
   if constexpr (SLRF_SPMM_STREAM == 0) {
-    stv<R>(p, v);
+    stv<R, V>(p, v);
   } else if constexpr (sizeof(R) == 8) {
     __stcs(reinterpret_cast<double2 *>(p), v.z[0]);
   } else {
 #pragma unroll
-    for (int j = 0; j < SLRF_F32_VEC / 2; ++j)
+    for (int j = 0; j < V / 2; ++j)
       __stcs(reinterpret_cast<float4 *>(p) + j,
              make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y));
   }
@@ -175,9 +176,9 @@ __device__ bool block_then_grid_reduce(double (&acc)[VEC][NQ], const int W, cons
 
 // ------------------------------------------------------------------------------ init
 // r0 = c g, p0 = r0, q0 = c (A g - sigma B g); reduce mu0 = p0^T q0, rho0 = r0^T r0, ||r0||^2.
-template <typename R>
+template <typename R, int V>
 __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int rb, const int tile) {
-  constexpr int VEC = cocg_vec<R>();
+  constexpr int VEC = V;
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
@@ -208,7 +209,7 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
   const int64_t i0 = (int64_t)rb * a.rows_per_block;
   const int64_t i1 = (i0 + a.rows_per_block < a.n ? i0 + a.rows_per_block : a.n);
   for (int64_t i = i0 + warp; i < i1; i += kWarps) {
-    Vec<R> rv, qv;
+    Vec<R, VEC> rv, qv;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
       R gv = 0, agv = 0, bgv = 0;
@@ -228,9 +229,9 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
     }
     const size_t off = (size_t)i * a.W + w0;
     if (CHK(2, off + VEC - 1, (long long)a.n * a.W)) {
-      stv<R>(a.r + off, rv);
-      stv<R>(a.p + off, rv);
-      stv<R>(a.q + off, qv);
+      stv<R, VEC>(a.r + off, rv);
+      stv<R, VEC>(a.p + off, rv);
+      stv<R, VEC>(a.q + off, qv);
     }
   }
   double out[NQ];
@@ -269,12 +270,12 @@ __device__ __forceinline__ void cocg_init_body(const CocgArgs<R> &a, const int r
 // n x k reals instead of d's n x k x m complex entries read and written every update.
 // Uacc is laid out tile by tile ([tile][row][columns of the tile]) so that each launch
 // streams it; the last update (kAccUEnd) writes U = coefV V + Uacc / gscale * dsc in FP64.
-template <typename R, bool FIRST, int FM>
+template <typename R, int V, bool FIRST, int FM>
 __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr bool ACCU_END = FM == kAccUEnd;
   constexpr bool ACCU = FM == kAccU || ACCU_END;
   constexpr bool FINAL = FM != kFinalNone && !ACCU;
-  constexpr int VEC = cocg_vec<R>();
+  constexpr int VEC = V;
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
@@ -305,7 +306,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
 #pragma unroll 1
   for (int64_t i = i0 + warp; i < i1; i += kWarps) {
     const size_t off = (size_t)i * a.W + w0;
-    Vec<R> dv;
+    Vec<R, VEC> dv;
     R step[VEC];  // kAccU: 2 Re(w_j alpha_j p_j) of this lane's entries
 #pragma unroll
     for (int v = 0; v < VEC; ++v) step[v] = R(0);
@@ -326,15 +327,15 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
 #pragma unroll
         for (int v = 0; v < VEC; ++v) dv.z[v] = cmake<C>(0, 0);
       } else if (any_act || FINAL) {
-        if (CHK(3, off + VEC - 1, (long long)a.n * a.W)) dv = ldv<R>(a.d + off);
+        if (CHK(3, off + VEC - 1, (long long)a.n * a.W)) dv = ldv<R, VEC>(a.d + off);
       }
     }
     if (any_act) {
-      Vec<R> pv, qv, rv;
+      Vec<R, VEC> pv, qv, rv;
       if (CHK(4, off + VEC - 1, (long long)a.n * a.W)) {
-        pv = ldv<R>(a.p + off);
-        qv = ldv<R>(a.q + off);
-        rv = ldv<R>(a.r + off);
+        pv = ldv<R, VEC>(a.p + off);
+        qv = ldv<R, VEC>(a.q + off);
+        rv = ldv<R, VEC>(a.r + off);
       }
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
@@ -352,7 +353,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
         acc[v][1] += 2 * rr.x * rr.y;
         acc[v][2] += rr.x * rr.x + rr.y * rr.y;
       }
-      if (CHK(5, off + VEC - 1, (long long)a.n * a.W)) stv<R>(a.r + off, rv);
+      if (CHK(5, off + VEC - 1, (long long)a.n * a.W)) stv<R, VEC>(a.r + off, rv);
     }
     if constexpr (ACCU) {
       if (FIRST || ACCU_END || warp_act) {
@@ -384,7 +385,7 @@ __device__ __forceinline__ void cocg_update_body(const CocgArgs<R> &a, const int
       }
       continue;
     }
-    if ((FIRST || any_act) && CHK(6, off + VEC - 1, (long long)a.n * a.W)) stv<R>(a.d + off, dv);
+    if ((FIRST || any_act) && CHK(6, off + VEC - 1, (long long)a.n * a.W)) stv<R, VEC>(a.d + off, dv);
     if (FM == kFinalStoreD || FM == kFinalAddD) {
       // refinement: accumulate this step's correction into the FP64 D
 #pragma unroll
@@ -526,9 +527,9 @@ __device__ __forceinline__ void spmm_tail(const CocgArgs<R> &a, const R (&acc)[V
 }
 
 // s = (A - sigma B) r; p = r + beta p; q = s + beta q; reduce mu = p^T q -> alpha = rho/mu.
-template <typename R, bool FRESH>
+template <typename R, int V, bool FRESH>
 __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int rb, const int tile) {
-  constexpr int VEC = cocg_vec<R>();
+  constexpr int VEC = V;
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
@@ -536,17 +537,10 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
   constexpr bool kSrec = sizeof(R) == 8 ? SLRF_SPMM_SREC64 != 0 : SLRF_SPMM_SREC32 != 0;
   __shared__ SRec<R> srec_all[kSrec ? kWarps * 32 : 1];
   SRec<R> *const srec = srec_all + (kSrec ? warp * 32 : 0);
-  C sg[VEC], be[VEC];
-  bool act[VEC];
+  // (beta and the poles are read again for each row's epilogue: not held across the gathers)
   bool any_act = false;
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) {
-    const WScal &s = a.ws[w0 + v];
-    act[v] = s.active != 0;
-    any_act |= act[v];
-    be[v] = to_c<R>(s.beta);
-    sg[v] = a.sig[(w0 + v) & (a.mp - 1)];
-  }
+  for (int v = 0; v < VEC; ++v) any_act |= a.ws[w0 + v].active != 0;
   // warp-uniform: skip the tile's SpMM when no column in it is still iterating
   const bool warp_act = __any_sync(0xffffffffu, any_act);
   constexpr int NQ = 2;
@@ -590,7 +584,7 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
             bv = __shfl_sync(0xffffffffu, bvl, t);
           }
           // byte offset c * W * sizeof(C) as one 32 x 32 -> 64-bit multiply-add (c >= 0)
-          const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
+          const Vec<R, VEC> x = ldv<R, VEC>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
             sa[v].x = fma(av, x.z[v].x, sa[v].x);
@@ -602,33 +596,35 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
       }
     };
     // p = r + beta p, q = s + beta q for the row, and its mu partial
-    auto finish_row = [&](int64_t i, const C (&sa)[VEC], const C (&sb)[VEC], const Vec<R> &rv, Vec<R> pv, Vec<R> qv) {
+    auto finish_row = [&](int64_t i, const C (&sa)[VEC], const C (&sb)[VEC], const Vec<R, VEC> &rv, Vec<R, VEC> pv, Vec<R, VEC> qv) {
       const size_t off = (size_t)i * a.W + w0;
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
-        const C s = cfms(sg[v], sb[v], sa[v]);  // A r - sigma B r
+        const C be = to_c<R>(a.ws[w0 + v].beta);
+        const C sg = a.sig[(w0 + v) & (a.mp - 1)];
+        const C s = cfms(sg, sb[v], sa[v]);  // A r - sigma B r
         // a fresh start (refinement step) has p = r and q = (A - sigma B) r
-        const C pn = FRESH ? rv.z[v] : cfma(be[v], pv.z[v], rv.z[v]);
-        const C qn = FRESH ? s : cfma(be[v], qv.z[v], s);
+        const C pn = FRESH ? rv.z[v] : cfma(be, pv.z[v], rv.z[v]);
+        const C qn = FRESH ? s : cfma(be, qv.z[v], s);
         pv.z[v] = pn;
         qv.z[v] = qn;
         acc[v][0] += pn.x * qn.x - pn.y * qn.y;
         acc[v][1] += pn.x * qn.y + pn.y * qn.x;
       }
-      stv_cs<R>(a.p + off, pv);
-      stv_cs<R>(a.q + off, qv);
+      stv_cs<R, VEC>(a.p + off, pv);
+      stv_cs<R, VEC>(a.q + off, qv);
     };
-    auto load_own = [&](int64_t i, Vec<R> &rv, Vec<R> &pv, Vec<R> &qv) {
+    auto load_own = [&](int64_t i, Vec<R, VEC> &rv, Vec<R, VEC> &pv, Vec<R, VEC> &qv) {
       const size_t off = (size_t)i * a.W + w0;
-      rv = ldv<R>(a.r + off);
+      rv = ldv<R, VEC>(a.r + off);
       if (!FRESH) {
-        pv = ldv_cs<R>(a.p + off);
-        qv = ldv_cs<R>(a.q + off);
+        pv = ldv_cs<R, VEC>(a.p + off);
+        qv = ldv_cs<R, VEC>(a.q + off);
       }
     };
     for (int64_t i = i0 + warp; i < i1; i += kWarps) {
       C sa[VEC], sb[VEC];
-      Vec<R> rv, pv, qv;
+      Vec<R, VEC> rv, pv, qv;
       gather_row(i, sa, sb);
       load_own(i, rv, pv, qv);
       finish_row(i, sa, sb, rv, pv, qv);
@@ -637,37 +633,177 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
   spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
 
-// s = (A - sigma B) r for groups of G consecutive rows that share one union column list
-// (grouped-row format, see CocgArgs): every gathered row of r feeds all G rows, so a row
-// costs union/G gathers instead of its own count (a 3-dof elasticity node: 27 instead of
-// 81).  Each warp walks its groups chunk by chunk (kGrpChunk records); lane 0 stages the
-// next chunk but one into the warp's other shared-memory buffer with a 1-D bulk copy, so
-// the records arrive through the TMA engine while the lanes gather and multiply.  All
-// lanes read a record with broadcast loads.  FP32: the complex products are packed FP32
-// FMAs on (a, a) x (re, im).  Waits are bounded (2 s, then *err and a drain of the
-// outstanding copies).
-template <typename R, int G, bool FRESH>
-__device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const int rb, const int tile) {
-  constexpr int VEC = cocg_vec<R>();
+// Record walk of the grouped-row SpMM for one warp (grouped-row format, see CocgArgs):
+// groups gfirst, gfirst + gstride, ... below ngroups.  Per group it accumulates, for this
+// lane's VEC pairs of the gathered row (x row c at xlane + c * xbytes),
+//   sa[j] += a_j(c) x_c,   sb[j] += b_j(c) x_c      (j < G, the group's rows)
+// over the group's records and then calls epi(g, sa, sb); sa and sb start at zero for every
+// group.  The records go chunk by chunk (kGrpChunk records) through the warp's two shared-
+// memory buffers: lane 0 stages the next chunk but one with a 1-D bulk copy, so the records
+// arrive through the TMA engine while the lanes gather and multiply; all lanes read a record
+// with broadcast loads.  FP32: packed FP32 FMAs on (a, a) x (x0, x1).  Waits are bounded
+// (2 s, then *err and a drain of the outstanding copies); a record whose column is out of
+// range sets *err = 3 and gathers row 0, inconsistent offsets set *err = 2.
+template <typename R, int V, int G, typename Epi>
+__device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *__restrict__ gptr,
+                                         const unsigned char *__restrict__ grec, int *err, const int64_t nx,
+                                         const int64_t gfirst, const int64_t gstride, const char *xlane,
+                                         const unsigned xbytes, unsigned char *sbuf, uint64_t *bar, Epi &&epi) {
+  constexpr int VEC = V;
   constexpr int RS = grec_bytes<G>();
   constexpr int CH = kGrpChunk;
+  using C = cx_t<R>;
+  const int lane = threadIdx.x & 31;
+  const int64_t gb1 = ngroups;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  auto nchunks = [&](int64_t g) -> int {
+    const int64_t c = gptr[g + 1] - gptr[g];
+    return c <= 0 ? 1 : (int)((c + CH - 1) / CH);
+  };
+  const int64_t nrec = gptr[ngroups];  // records in all (bounds of every copy)
+  auto first = [&](int64_t g, int c, int &cnt) -> int64_t {
+    const int64_t e0 = gptr[g] + (int64_t)c * CH, e1 = gptr[g + 1];
+    cnt = (int)(e1 - e0 < CH ? e1 - e0 : CH);
+    if (cnt < 0 || e0 < 0 || e0 + cnt > nrec) {
+      if (cnt != 0) atomicCAS(err, 0, 2);  // inconsistent offsets: copy nothing
+      cnt = 0;
+    }
+    return e0;
+  };
+  auto issue = [&](int b, int64_t g, int c) {
+    if (lane == 0) {
+      int cnt;
+      const int64_t e0 = first(g, c, cnt);
+      // the lanes' shared-memory reads of this buffer (ordered by the __syncwarp before
+      // the call) precede the asynchronous proxy's writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (cnt > 0) {
+        mbar_expect_tx(bar + b, (uint32_t)(cnt * RS));
+        bulk_g2s(sbuf + (size_t)b * CH * RS, grec + (size_t)e0 * RS, (uint32_t)(cnt * RS), bar + b);
+      } else {
+        mbar_arrive(bar + b);
+      }
+    }
+  };
+  int64_t cg = gfirst, ng = cg;  // current item (group, chunk), next item
+  int cc = 0, nc = 0;
+  auto advance = [&](int64_t &g, int &c) {
+    if (c + 1 < nchunks(g)) ++c;
+    else { g += gstride; c = 0; }
+  };
+  issue(0, cg, cc);
+  advance(ng, nc);
+  if (ng < gb1) issue(1, ng, nc);
+  uint32_t ph0 = 0, ph1 = 0;
+  int b = 0;
+  bool failed = false;
+  C sa[G][VEC], sb[G][VEC];
+#pragma unroll
+  for (int j = 0; j < G; ++j)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
+  while (cg < gb1) {
+    if (!mbar_wait(bar + b, b ? ph1 : ph0, err, 1)) { failed = true; break; }
+    if (b) ph1 ^= 1u; else ph0 ^= 1u;
+    int cnt;
+    first(cg, cc, cnt);
+    const unsigned char *rb_ = sbuf + (size_t)b * CH * RS;
+#pragma unroll kGrpUnroll
+    for (int t = 0; t < cnt; ++t) {
+      const unsigned char *rp = rb_ + t * RS;
+      int c = *reinterpret_cast<const int *>(rp + 16 * G);
+      if ((unsigned)c >= (unsigned)nx) {  // a corrupt record: flag it, gather row 0
+        atomicCAS(err, 0, 3);
+        (void)CHK(21, c, nx);
+        c = 0;
+      }
+      const Vec<R, VEC> x = ldv<R, VEC>(reinterpret_cast<const C *>(xlane + (unsigned long long)(unsigned)c * xbytes));
+      // the record's 2 G values in G 16-byte broadcast loads
+      float4 rv4[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) rv4[j] = reinterpret_cast<const float4 *>(rp)[j];
+      const float *rvf = reinterpret_cast<const float *>(rv4);
+      if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const float2 av = make_float2(rvf[2 * j], rvf[2 * j + 1]);
+          const float2 bv = make_float2(rvf[2 * (G + j)], rvf[2 * (G + j) + 1]);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            sa[j][v] = ffma2(av, x.z[v], sa[j][v]);
+            sb[j][v] = ffma2(bv, x.z[v], sb[j][v]);
+          }
+        }
+      } else {
+        const double *rvd = reinterpret_cast<const double *>(rv4);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const double av = rvd[j];
+          const double bv = rvd[G + j];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            sa[j][v].x = fma(av, x.z[v].x, sa[j][v].x);
+            sa[j][v].y = fma(av, x.z[v].y, sa[j][v].y);
+            sb[j][v].x = fma(bv, x.z[v].x, sb[j][v].x);
+            sb[j][v].y = fma(bv, x.z[v].y, sb[j][v].y);
+          }
+        }
+      }
+    }
+    if (cc + 1 >= nchunks(cg)) {
+      epi(cg, sa, sb);  // the group's last chunk
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
+    }
+    __syncwarp();
+    // stage the item after next into the buffer just read
+    int64_t g2 = ng;
+    int c2 = nc;
+    if (g2 < gb1) {
+      advance(g2, c2);
+      if (g2 < gb1) issue(b, g2, c2);
+    }
+    cg = ng;
+    cc = nc;
+    ng = g2;
+    nc = c2;
+    b ^= 1;
+  }
+  if (failed) {
+    // wait (bounded) for the copies this warp may still have in flight, then leave
+    if (lane == 0) {
+      mbar_wait(bar + b, b ? ph1 : ph0, err, 1);
+      if (ng < gb1) mbar_wait(bar + (b ^ 1), b ? ph0 : ph1, err, 1);
+    }
+    __syncwarp();
+  }
+}
+
+// s = (A - sigma B) r for groups of G consecutive rows that share one union column list
+// (grouped-row format): every gathered row of r feeds all G rows, so a row costs union/G
+// gathers instead of its own count (a 3-dof elasticity node: 27 instead of 81).  Then, per
+// row, p = r + beta p, q = s + beta q and the mu partials.
+template <typename R, int V, int G, bool FRESH>
+__device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const int rb, const int tile) {
+  constexpr int VEC = V;
+  constexpr int RS = grec_bytes<G>();
   using C = cx_t<R>;
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
   const int w0 = w_tile0 + lane * VEC;
-  unsigned char *const sbuf = grp_smem + (size_t)warp * 2 * CH * RS;
-  uint64_t *const bar = s_bar[warp];
-  C sg[VEC], be[VEC];
+  // (beta and the poles are read again in each group's epilogue: not held across the walk)
   bool any_act = false;
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) {
-    const WScal &s = a.ws[w0 + v];
-    any_act |= s.active != 0;
-    be[v] = to_c<R>(s.beta);
-    sg[v] = a.sig[(w0 + v) & (a.mp - 1)];
-  }
+  for (int v = 0; v < VEC; ++v) any_act |= a.ws[w0 + v].active != 0;
   const bool warp_act = __any_sync(0xffffffffu, any_act);
   R acc[VEC][2];
 #pragma unroll
@@ -678,165 +814,45 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
   // the groups that need it while it is still in L2, also when one column tile of r is
   // larger than L2 (nrb is one resident wave of this kernel).
   const int64_t gstride = (int64_t)a.nrb * kWarps;
-  const int64_t gb1 = a.ngroups;
   const int64_t gfirst = (int64_t)rb * kWarps + warp;
-  if (warp_act && gfirst < gb1) {
-    if (lane == 0) {
-      mbar_init(bar, 1);
-      mbar_init(bar + 1, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    const char *const rlane = reinterpret_cast<const char *>(a.r + w0);
-    const unsigned wbytes = (unsigned)a.W * (unsigned)sizeof(C);
-    // work items (group, chunk) of this warp: groups gfirst, + gstride, ...
-    auto nchunks = [&](int64_t g) -> int {
-      const int64_t c = a.gptr[g + 1] - a.gptr[g];
-      return c <= 0 ? 1 : (int)((c + CH - 1) / CH);
-    };
-    const int64_t nrec = a.gptr[a.ngroups];  // records in all (bounds of every copy)
-    auto first = [&](int64_t g, int c, int &cnt) -> int64_t {
-      const int64_t e0 = a.gptr[g] + (int64_t)c * CH, e1 = a.gptr[g + 1];
-      cnt = (int)(e1 - e0 < CH ? e1 - e0 : CH);
-      if (cnt < 0 || e0 < 0 || e0 + cnt > nrec) {
-        if (cnt != 0) atomicCAS(a.err, 0, 2);  // inconsistent offsets: copy nothing
-        cnt = 0;
+  if (warp_act && gfirst < a.ngroups) {
+    auto epi = [&](int64_t g, const C (&sa)[G][VEC], const C (&sb)[G][VEC]) {
+      C sg[VEC], be[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        be[v] = to_c<R>(a.ws[w0 + v].beta);
+        sg[v] = a.sig[(w0 + v) & (a.mp - 1)];
       }
-      return e0;
-    };
-    auto issue = [&](int b, int64_t g, int c) {
-      if (lane == 0) {
-        int cnt;
-        const int64_t e0 = first(g, c, cnt);
-        // the lanes' shared-memory reads of this buffer (ordered by the __syncwarp before
-        // the call) precede the asynchronous proxy's writes
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (cnt > 0) {
-          mbar_expect_tx(bar + b, (uint32_t)(cnt * RS));
-          bulk_g2s(sbuf + (size_t)b * CH * RS, a.grec + (size_t)e0 * RS, (uint32_t)(cnt * RS), bar + b);
-        } else {
-          mbar_arrive(bar + b);
-        }
-      }
-    };
-    int64_t cg = gfirst, ng = cg;  // current item, next item
-    int cc = 0, nc = 0;
-    auto advance = [&](int64_t &g, int &c) {
-      if (c + 1 < nchunks(g)) ++c;
-      else { g += gstride; c = 0; }
-    };
-    issue(0, cg, cc);
-    advance(ng, nc);
-    if (ng < gb1) issue(1, ng, nc);
-    uint32_t ph0 = 0, ph1 = 0;
-    int b = 0;
-    bool failed = false;
-    C sa[G][VEC], sb[G][VEC];
 #pragma unroll
-    for (int j = 0; j < G; ++j)
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
-    while (cg < gb1) {
-      if (!mbar_wait(bar + b, b ? ph1 : ph0, a.err, 1)) { failed = true; break; }
-      if (b) ph1 ^= 1u; else ph0 ^= 1u;
-      int cnt;
-      first(cg, cc, cnt);
-      const unsigned char *rb_ = sbuf + (size_t)b * CH * RS;
-#pragma unroll kGrpUnroll
-      for (int t = 0; t < cnt; ++t) {
-        const unsigned char *rp = rb_ + t * RS;
-        int c = *reinterpret_cast<const int *>(rp + 16 * G);
-        if ((unsigned)c >= (unsigned)a.n) {  // a corrupt record: flag it, gather row 0
-          atomicCAS(a.err, 0, 3);
-          (void)CHK(21, c, a.n);
-          c = 0;
-        }
-        const Vec<R> x = ldv<R>(reinterpret_cast<const C *>(rlane + (unsigned long long)(unsigned)c * wbytes));
-        // the record's 2 G values in G 16-byte broadcast loads
-        float4 rv4[G];
-#pragma unroll
-        for (int j = 0; j < G; ++j) rv4[j] = reinterpret_cast<const float4 *>(rp)[j];
-        const float *rvf = reinterpret_cast<const float *>(rv4);
-        if constexpr (sizeof(R) == 4) {
-#pragma unroll
-          for (int j = 0; j < G; ++j) {
-            const float2 av = make_float2(rvf[2 * j], rvf[2 * j + 1]);
-            const float2 bv = make_float2(rvf[2 * (G + j)], rvf[2 * (G + j) + 1]);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              sa[j][v] = ffma2(av, x.z[v], sa[j][v]);
-              sb[j][v] = ffma2(bv, x.z[v], sb[j][v]);
-            }
-          }
-        } else {
-          const double *rvd = reinterpret_cast<const double *>(rv4);
-#pragma unroll
-          for (int j = 0; j < G; ++j) {
-            const double av = rvd[j];
-            const double bv = rvd[G + j];
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              sa[j][v].x = fma(av, x.z[v].x, sa[j][v].x);
-              sa[j][v].y = fma(av, x.z[v].y, sa[j][v].y);
-              sb[j][v].x = fma(bv, x.z[v].x, sb[j][v].x);
-              sb[j][v].y = fma(bv, x.z[v].y, sb[j][v].y);
-            }
-          }
-        }
-      }
-      if (cc + 1 >= nchunks(cg)) {
-        // last chunk of the group: p = r + beta p, q = s + beta q for its rows, mu partials
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const int64_t i = cg * G + j;
-          if (i < a.n) {
-            const size_t off = (size_t)i * a.W + w0;
-            if (!CHK(20, off + VEC - 1, (long long)a.n * a.W)) continue;
-            const Vec<R> rv = ldv<R>(a.r + off);
-            Vec<R> pv, qv;
-            if (!FRESH) {
-              pv = ldv_cs<R>(a.p + off);
-              qv = ldv_cs<R>(a.q + off);
-            }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              const C sv = cfms(sg[v], sb[j][v], sa[j][v]);  // A r - sigma B r
-              const C pn = FRESH ? rv.z[v] : cfma(be[v], pv.z[v], rv.z[v]);
-              const C qn = FRESH ? sv : cfma(be[v], qv.z[v], sv);
-              pv.z[v] = pn;
-              qv.z[v] = qn;
-              acc[v][0] += pn.x * qn.x - pn.y * qn.y;
-              acc[v][1] += pn.x * qn.y + pn.y * qn.x;
-            }
-            stv_cs<R>(a.p + off, pv);
-            stv_cs<R>(a.q + off, qv);
+      for (int j = 0; j < G; ++j) {
+        const int64_t i = g * G + j;
+        if (i < a.n) {
+          const size_t off = (size_t)i * a.W + w0;
+          if (!CHK(20, off + VEC - 1, (long long)a.n * a.W)) continue;
+          const Vec<R, VEC> rv = ldv<R, VEC>(a.r + off);
+          Vec<R, VEC> pv, qv;
+          if (!FRESH) {
+            pv = ldv_cs<R, VEC>(a.p + off);
+            qv = ldv_cs<R, VEC>(a.q + off);
           }
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) { sa[j][v] = cmake<C>(0, 0); sb[j][v] = cmake<C>(0, 0); }
+          for (int v = 0; v < VEC; ++v) {
+            const C sv = cfms(sg[v], sb[j][v], sa[j][v]);  // A r - sigma B r
+            const C pn = FRESH ? rv.z[v] : cfma(be[v], pv.z[v], rv.z[v]);
+            const C qn = FRESH ? sv : cfma(be[v], qv.z[v], sv);
+            pv.z[v] = pn;
+            qv.z[v] = qn;
+            acc[v][0] += pn.x * qn.x - pn.y * qn.y;
+            acc[v][1] += pn.x * qn.y + pn.y * qn.x;
+          }
+          stv_cs<R, VEC>(a.p + off, pv);
+          stv_cs<R, VEC>(a.q + off, qv);
         }
       }
-      __syncwarp();
-      // stage the item after next into the buffer just read
-      int64_t g2 = ng;
-      int c2 = nc;
-      if (g2 < gb1) {
-        advance(g2, c2);
-        if (g2 < gb1) issue(b, g2, c2);
-      }
-      cg = ng;
-      cc = nc;
-      ng = g2;
-      nc = c2;
-      b ^= 1;
-    }
-    if (failed) {
-      // wait (bounded) for the copies this warp may still have in flight, then leave
-      if (lane == 0) {
-        mbar_wait(bar + b, b ? ph1 : ph0, a.err, 1);
-        if (ng < gb1) mbar_wait(bar + (b ^ 1), b ? ph0 : ph1, a.err, 1);
-      }
-      __syncwarp();
-    }
+    };
+    grp_walk<R, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
+                   reinterpret_cast<const char *>(a.r + w0), (unsigned)a.W * (unsigned)sizeof(C),
+                   grp_smem + (size_t)warp * 2 * kGrpChunk * RS, s_bar[warp], epi);
   }
   spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
@@ -847,9 +863,9 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
 // written as the new FP32 right-hand side r (p and q follow in the fresh SpMM); new
 // scalars rho = R^T R, ||R||^2 per w.  Every column with a nonzero residual (and no
 // earlier breakdown) is refined; its FP32 solve stops at tol ||R|| or It_max.
-template <typename R>
+template <typename R, int V>
 __device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const int rb, const int tile) {
-  constexpr int VEC = cocg_vec<R>();
+  constexpr int VEC = V;
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_tile0 = tile * 32 * VEC;
@@ -905,7 +921,7 @@ __device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const i
       }
     }
     const size_t off = (size_t)i * a.W + w0;
-    Vec<R> rv;
+    Vec<R, VEC> rv;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
       const double g = ok[v] ? a.g[(size_t)i * a.ldg + cidx[v]] : 0.0;
@@ -921,7 +937,7 @@ __device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const i
       acc[v][1] += 2.0 * rx * ry;
       acc[v][2] += rx * rx + ry * ry;
     }
-    stv<R>(a.r + off, rv);
+    stv<R, VEC>(a.r + off, rv);
   }
   double out[NQ];
   int w;
@@ -943,13 +959,13 @@ __device__ __forceinline__ void cocg_residual_body(const CocgArgs<R> &a, const i
 
 // ------------------------------------------------------------------------------ kernels
 // Single problem: blockIdx.x = row block, blockIdx.y = tile.
-template <typename R>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_init_kernel(const CocgArgs<R> a) {
-  cocg_init_body<R>(a, blockIdx.x, blockIdx.y);
+template <typename R, int V>
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, V>())) cocg_init_kernel(const CocgArgs<R> a) {
+  cocg_init_body<R, V>(a, blockIdx.x, blockIdx.y);
 }
-template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(const CocgArgs<R> a, int tile0) {
-  cocg_update_body<R, FIRST, FM>(a, blockIdx.x, tile0 + blockIdx.y);
+template <typename R, int V, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, V>())) cocg_update_kernel(const CocgArgs<R> a, int tile0) {
+  cocg_update_body<R, V, FIRST, FM>(a, blockIdx.x, tile0 + blockIdx.y);
 }
 // Two groups of tiles in one launch: the SpMM of tiles [s0, s0 + ns) and the update of tiles
 // [u0, u0 + nu).  Tiles are independent systems (own scalars, partial slots and counters),
@@ -957,11 +973,11 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_kernel(c
 // in FP32), the update by HBM.  Blocks alternate between the two kinds so that both are
 // resident from the start; within each kind the row block varies fastest.
 // resident blocks per SM of the grouped SpMM (more registers: G rows of accumulators)
-template <typename R, int G> __host__ __device__ constexpr int cocg_grp_minb() {
-  return G == 1 ? cocg_minb<R>() : SLRF_GRP_MINB;
+template <typename R, int V, int G> __host__ __device__ constexpr int cocg_grp_minb() {
+  return G == 1 ? cocg_minb<R, V>() : SLRF_GRP_MINB;
 }
-template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(const CocgArgs<R> a, int s0, int ns,
+template <typename R, int V, bool FIRST, int FM>
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, V>())) cocg_dual_kernel(const CocgArgs<R> a, int s0, int ns,
                                                                               int u0, int nu) {
   const int NS = a.nrb * ns, NU = a.nrb * nu;
   const int both = 2 * (NS < NU ? NS : NU);
@@ -975,20 +991,20 @@ __global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_dual_kernel(con
     spmm = NS > NU;
     item = (b - both) + (NS < NU ? NS : NU);
   }
-  if (spmm) cocg_spmm_body<R, false>(a, item % a.nrb, s0 + item / a.nrb);
-  else cocg_update_body<R, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
+  if (spmm) cocg_spmm_body<R, V, false>(a, item % a.nrb, s0 + item / a.nrb);
+  else cocg_update_body<R, V, FIRST, FM>(a, item % a.nrb, u0 + item / a.nrb);
 }
-template <typename R, bool FRESH>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_kernel(const CocgArgs<R> a) {
-  cocg_spmm_body<R, FRESH>(a, blockIdx.x, blockIdx.y);
+template <typename R, int V, bool FRESH>
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, V>())) cocg_spmm_kernel(const CocgArgs<R> a) {
+  cocg_spmm_body<R, V, FRESH>(a, blockIdx.x, blockIdx.y);
 }
-template <typename R, int G, bool FRESH>
-__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, G>())) cocg_spmm_grp_kernel(const CocgArgs<R> a) {
-  cocg_spmm_grp_body<R, G, FRESH>(a, blockIdx.x, blockIdx.y);
+template <typename R, int V, int G, bool FRESH>
+__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, V, G>())) cocg_spmm_grp_kernel(const CocgArgs<R> a) {
+  cocg_spmm_grp_body<R, V, G, FRESH>(a, blockIdx.x, blockIdx.y);
 }
-template <typename R>
+template <typename R, int V>
 __global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
-  cocg_residual_body<R>(a, blockIdx.x, blockIdx.y);
+  cocg_residual_body<R, V>(a, blockIdx.x, blockIdx.y);
 }
 
 // Many problems in one persistent launch: work item t of the list belongs to problem p
@@ -1012,21 +1028,22 @@ __device__ __forceinline__ int batch_problem(const int *prefix, int P, int item)
     BODY;                                                                   \
     __syncthreads();                                                        \
   }
+// (the batched path runs plain CSR only: lane width cocg_vec_csr<R>(), checked by the host)
 template <typename R>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_init_batched(const CocgArgs<R> *args, const int *prefix, int P) {
-  SLRF_BATCH_LOOP((cocg_init_body<R>(a, local % a.nrb, local / a.nrb)))
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, cocg_vec_csr<R>()>())) cocg_init_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_init_body<R, cocg_vec_csr<R>()>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R, bool FIRST, int FM>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_update_batched(const CocgArgs<R> *args, const int *prefix, int P) {
-  SLRF_BATCH_LOOP((cocg_update_body<R, FIRST, FM>(a, local % a.nrb, local / a.nrb)))
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, cocg_vec_csr<R>()>())) cocg_update_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_update_body<R, cocg_vec_csr<R>(), FIRST, FM>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R, bool FRESH>
-__global__ void __launch_bounds__(kThreads, cocg_minb<R>()) cocg_spmm_batched(const CocgArgs<R> *args, const int *prefix, int P) {
-  SLRF_BATCH_LOOP((cocg_spmm_body<R, FRESH>(a, local % a.nrb, local / a.nrb)))
+__global__ void __launch_bounds__(kThreads, (cocg_minb<R, cocg_vec_csr<R>()>())) cocg_spmm_batched(const CocgArgs<R> *args, const int *prefix, int P) {
+  SLRF_BATCH_LOOP((cocg_spmm_body<R, cocg_vec_csr<R>(), FRESH>(a, local % a.nrb, local / a.nrb)))
 }
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 2) cocg_residual_batched(const CocgArgs<R> *args, const int *prefix, int P) {
-  SLRF_BATCH_LOOP((cocg_residual_body<R>(a, local % a.nrb, local / a.nrb)))
+  SLRF_BATCH_LOOP((cocg_residual_body<R, cocg_vec_csr<R>()>(a, local % a.nrb, local / a.nrb)))
 }
 #undef SLRF_BATCH_LOOP
 
@@ -1181,25 +1198,40 @@ void cocg_prepare(int W, int k, int m, int mp, const double2 *sig, const double2
 }
 
 template <typename R> static dim3 grid_of(const CocgArgs<R> &a) {
-  return dim3((unsigned)a.nrb, (unsigned)(a.W / (32 * cocg_vec<R>())));
+  return dim3((unsigned)a.nrb, (unsigned)(a.W / (32 * a.vec)));
 }
-
-template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
-  cocg_init_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
+// Calls f(std::integral_constant<int, V>) with the lane width a.vec as a constant.
+template <typename R, typename F> static void with_vec(const CocgArgs<R> &a, F &&f) {
+  if constexpr (sizeof(R) == 8) {
+    f(std::integral_constant<int, 1>{});
+  } else {
+    if (a.vec == 4) f(std::integral_constant<int, 4>{});
+    else f(std::integral_constant<int, 2>{});
+  }
 }
-// A mode whose buffers are missing launches nothing: code 4 in *a.err (status SLRF_EINVAL)
-template <typename R> static bool mode_guard(const CocgArgs<R> &a, int fm, cudaStream_t st) {
-  if (cocg_mode_ok(a, fm)) return true;
+// Arguments a launch cannot use launch nothing: code 4 in *a.err (status SLRF_EINVAL).
+template <typename R> static bool refuse(const CocgArgs<R> &a, cudaStream_t st) {
   // low byte only (a memset is allowed under stream capture); the flag starts at zero
   if (a.err != nullptr) cudaMemsetAsync(a.err, 4, 1, st);
   return false;
 }
-template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st, int tile0,
-                                      int ntiles) {
-  if (!mode_guard(a, fm, st)) return;
-  dim3 g = grid_of(a);
-  if (ntiles > 0) g.y = (unsigned)ntiles;
-#define UPD(F, M) cocg_update_kernel<R, F, M><<<g, kThreads, 0, st>>>(a, tile0)
+template <typename R> static bool args_guard(const CocgArgs<R> &a, cudaStream_t st) {
+  return cocg_layout_ok(a) ? true : refuse(a, st);
+}
+template <typename R> static bool mode_guard(const CocgArgs<R> &a, int fm, cudaStream_t st) {
+  return (cocg_layout_ok(a) && cocg_mode_ok(a, fm)) ? true : refuse(a, st);
+}
+
+template <typename R> void cocg_init(const CocgArgs<R> &a, cudaStream_t st) {
+  if (!args_guard(a, st)) return;
+  with_vec(a, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    cocg_init_kernel<R, V><<<grid_of(a), kThreads, 0, st>>>(a);
+  });
+}
+template <typename R, int V>
+static void update_launch(const CocgArgs<R> &a, bool first, int fm, dim3 g, int tile0, cudaStream_t st) {
+#define UPD(F, M) cocg_update_kernel<R, V, F, M><<<g, kThreads, 0, st>>>(a, tile0)
   if (first) {
     switch (fm) {
       case kFinalNone: UPD(true, kFinalNone); break;
@@ -1223,11 +1255,17 @@ template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm,
   }
 #undef UPD
 }
-template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
-                                    cudaStream_t st) {
+template <typename R> void cocg_update(const CocgArgs<R> &a, bool first, int fm, cudaStream_t st, int tile0,
+                                      int ntiles) {
   if (!mode_guard(a, fm, st)) return;
+  dim3 g = grid_of(a);
+  if (ntiles > 0) g.y = (unsigned)ntiles;
+  with_vec(a, [&](auto vc) { update_launch<R, decltype(vc)::value>(a, first, fm, g, tile0, st); });
+}
+template <typename R, int V>
+static void dual_launch(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm, cudaStream_t st) {
   const unsigned blocks = (unsigned)a.nrb * (unsigned)(ns + nu);
-#define DUAL(F, M) cocg_dual_kernel<R, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
+#define DUAL(F, M) cocg_dual_kernel<R, V, F, M><<<blocks, kThreads, 0, st>>>(a, s0, ns, u0, nu)
   if (first) {
     if (fm == kAccU) DUAL(true, kAccU);
     else DUAL(true, kFinalNone);  // a group's first update is never its last (It_max >= 2)
@@ -1244,28 +1282,126 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
   }
 #undef DUAL
 }
-template <typename R, int G> static void cocg_spmm_grp(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
-  if (fresh) cocg_spmm_grp_kernel<R, G, true><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
-  else cocg_spmm_grp_kernel<R, G, false><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u0, int nu, bool first, int fm,
+                                    cudaStream_t st) {
+  if (!mode_guard(a, fm, st)) return;
+  with_vec(a, [&](auto vc) { dual_launch<R, decltype(vc)::value>(a, s0, ns, u0, nu, first, fm, st); });
 }
-
-template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+template <typename R, int V, int G> static void spmm_grp_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+  if (fresh) cocg_spmm_grp_kernel<R, V, G, true><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+  else cocg_spmm_grp_kernel<R, V, G, false><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+}
+template <typename R, int V> static void spmm_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   switch (a.G) {
-    case 2: cocg_spmm_grp<R, 2>(a, st, fresh); return;
-    case 3: cocg_spmm_grp<R, 3>(a, st, fresh); return;
-    case 4: cocg_spmm_grp<R, 4>(a, st, fresh); return;
+    case 2: spmm_grp_launch<R, V, 2>(a, st, fresh); return;
+    case 3: spmm_grp_launch<R, V, 3>(a, st, fresh); return;
+    case 4: spmm_grp_launch<R, V, 4>(a, st, fresh); return;
     default: break;
   }
-  if (fresh) cocg_spmm_kernel<R, true><<<grid_of(a), kThreads, 0, st>>>(a);
-  else cocg_spmm_kernel<R, false><<<grid_of(a), kThreads, 0, st>>>(a);
+  if (fresh) cocg_spmm_kernel<R, V, true><<<grid_of(a), kThreads, 0, st>>>(a);
+  else cocg_spmm_kernel<R, V, false><<<grid_of(a), kThreads, 0, st>>>(a);
+}
+template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
+  if (!args_guard(a, st)) return;
+  with_vec(a, [&](auto vc) { spmm_launch<R, decltype(vc)::value>(a, st, fresh); });
 }
 
 // Dynamic shared memory above the default 48 KB for every grouped kernel instance
 // (called once per process, before any launch or stream capture).
-template <typename R, int G> static void grp_attrs() {
+// ------------------------------------------------------------------------------ real SpMM
+// Real products through the FP32 grouped records: each lane takes VEC pairs of adjacent real
+// columns of x32, so the packed FMA (a, a) x (x_c, x_c+1) of the complex SpMM serves two real
+// columns at once.  Grid (row blocks, column tiles of 64 VEC real columns); interleaved
+// stripes as in the COCG SpMM.
+constexpr int kReal32Vec = 4;  // pairs of real columns per lane
+int grp_real32_ld(int k) {
+  const int t = 64 * kReal32Vec;
+  return (k + t - 1) / t * t;
+}
+__global__ void to_f32_scaled_kernel(int64_t n, int k, const double *__restrict__ X, int ldx,
+                                     const double *__restrict__ s, float *__restrict__ Y, int ldy) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ldy) return;
+  const int64_t i = t / ldy;
+  const int c = (int)(t - i * ldy);
+  Y[t] = c < k ? (float)(s != nullptr ? X[i * ldx + c] * s[i] : X[i * ldx + c]) : 0.f;
+}
+struct GrpReal32 {
+  int64_t n, ngroups;
+  const int64_t *gptr;
+  const unsigned char *grec;
+  int *err;
+  int nrb;
+  const float *x;
+  int ldx;
+  int k;
+  double *YA, *YB;
+  int ldy;
+  const double *yscale;
+};
+template <int G>
+__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>())) spmm_grp_real32_kernel(const GrpReal32 a) {
+  constexpr int VEC = kReal32Vec;
+  constexpr int RS = grec_bytes<G>();
+  extern __shared__ __align__(128) unsigned char grp_smem[];
+  __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = (int)blockIdx.y * 64 * VEC + lane * 2 * VEC;  // this lane's first real column
+  const int64_t gstride = (int64_t)a.nrb * kWarps;
+  const int64_t gfirst = (int64_t)blockIdx.x * kWarps + warp;
+  if (gfirst >= a.ngroups) return;  // warp-uniform; the kernel has no block-wide barrier
+  auto epi = [&](int64_t g, const float2 (&sa)[G][VEC], const float2 (&sb)[G][VEC]) {
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const int64_t i = g * G + j;
+      if (i >= a.n) continue;
+      const double ys = a.yscale != nullptr ? a.yscale[i] : 1.0;
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = c0 + 2 * v + e;
+          if (c < a.k) {
+            if (a.YA) a.YA[(size_t)i * a.ldy + c] = ys * (double)(e ? sa[j][v].y : sa[j][v].x);
+            if (a.YB) a.YB[(size_t)i * a.ldy + c] = ys * (double)(e ? sb[j][v].y : sb[j][v].x);
+          }
+        }
+    }
+  };
+  grp_walk<float, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
+                     reinterpret_cast<const char *>(a.x + c0), (unsigned)a.ldx * 4u,
+                     grp_smem + (size_t)warp * 2 * kGrpChunk * RS, s_bar[warp], epi);
+}
+void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err,
+                     int nrb, const double *X, int ldx, int k, const double *xscale, float *x32, double *YA,
+                     double *YB, int ldy, const double *yscale, cudaStream_t st) {
+  if (n <= 0 || k <= 0 || nrb <= 0) return;
+  const int ld32 = grp_real32_ld(k);
+  const int64_t tot = n * ld32;
+  to_f32_scaled_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, X, ldx, xscale, x32, ld32);
+  GrpReal32 a{n, ngroups, gptr, grec, err, nrb, x32, ld32, k, YA, YB, ldy, yscale};
+  const dim3 grid((unsigned)nrb, (unsigned)(ld32 / (64 * kReal32Vec)));
+  switch (G) {
+    case 2: spmm_grp_real32_kernel<2><<<grid, kThreads, grp_smem_bytes<2>(), st>>>(a); break;
+    case 3: spmm_grp_real32_kernel<3><<<grid, kThreads, grp_smem_bytes<3>(), st>>>(a); break;
+    case 4: spmm_grp_real32_kernel<4><<<grid, kThreads, grp_smem_bytes<4>(), st>>>(a); break;
+    default: break;
+  }
+}
+
+template <typename R, int V, int G> static void grp_attrs_v() {
   const int sm = grp_smem_bytes<G>();
-  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+template <typename R, int G> static void grp_attrs() {
+  if constexpr (sizeof(R) == 8) {
+    grp_attrs_v<R, 1, G>();
+  } else {
+    grp_attrs_v<R, 2, G>();
+    grp_attrs_v<R, 4, G>();
+    cudaFuncSetAttribute(spmm_grp_real32_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, grp_smem_bytes<G>());
+  }
 }
 void cocg_kernel_attrs() {
   static bool done = false;
@@ -1281,7 +1417,7 @@ void cocg_kernel_attrs() {
 }
 template <typename R, int G> static int grp_occ() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, G, false>, kThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, cocg_vec_grp<R>(), G, false>, kThreads,
                                                     grp_smem_bytes<G>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1297,7 +1433,11 @@ int grp_blocks_per_sm(int G, bool fp32) {
   }
 }
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st) {
-  cocg_residual_kernel<R><<<grid_of(a), kThreads, 0, st>>>(a);
+  if (!args_guard(a, st)) return;
+  with_vec(a, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    cocg_residual_kernel<R, V><<<grid_of(a), kThreads, 0, st>>>(a);
+  });
 }
 
 template void cocg_init<double>(const CocgArgs<double> &, cudaStream_t);

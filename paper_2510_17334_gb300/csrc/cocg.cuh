@@ -29,7 +29,9 @@ struct CocgArgs {
   const int32_t *col;
   const R *valA;
   const R *valB;
-  int W;        // complex entries per row: kpad * mp, a multiple of 32 * VEC
+  int W;        // complex entries per row: kpad * mp, a multiple of 32 * vec
+  int vec;      // complex entries per lane (the tile is 32 vec entries): FP64 1; FP32 2
+                // with the plain CSR SpMM, 4 with the grouped one (cocg_vec_csr / _grp)
   int k;        // real columns in the block
   int m;        // poles in use
   int mp;       // poles padded to a power of two (<= 32)
@@ -124,16 +126,29 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
 template <typename R> void cocg_spmm(const CocgArgs<R> &a, cudaStream_t st, bool fresh = false);
 // refinement step s >= 2: r = r0 - (A - sigma B) D (FP64), new COCG scalars per w
 template <typename R> void cocg_residual(const CocgArgs<R> &a, cudaStream_t st);
-// complex entries per lane: one 16-byte value in FP64, SLRF_F32_VEC (two 16-byte loads) in FP32
-#ifndef SLRF_F32_VEC
-#define SLRF_F32_VEC 2
-#endif
-template <typename R> __host__ __device__ constexpr int cocg_vec() { return sizeof(R) == 8 ? 1 : SLRF_F32_VEC; }
+// Complex entries per lane (CocgArgs::vec): one 16-byte value in FP64; in FP32 two (one
+// 16-byte load) with the plain CSR SpMM and four (two loads) with the grouped-row SpMM,
+// whose staged records then serve twice the columns.  Measured on GB300: four entries make
+// the grouped SpMM of the 64 x 64 x 32 elasticity box 16 % faster and the plain CSR SpMM of
+// the 41^3 Laplacian 20 % slower.
+template <typename R> __host__ __device__ constexpr int cocg_vec_csr() { return sizeof(R) == 8 ? 1 : 2; }
+template <typename R> __host__ __device__ constexpr int cocg_vec_grp() { return sizeof(R) == 8 ? 1 : 4; }
+template <typename R> __host__ __device__ constexpr int cocg_vec_max() { return sizeof(R) == 8 ? 1 : 4; }
 // resident blocks per SM the COCG kernels are compiled for (sets their register budget)
 #ifndef SLRF_F32_MINB
 #define SLRF_F32_MINB 4
 #endif
-template <typename R> __host__ __device__ constexpr int cocg_minb() { return sizeof(R) == 8 ? 4 : SLRF_F32_MINB; }
+#ifndef SLRF_F32_MINB4
+#define SLRF_F32_MINB4 3
+#endif
+template <typename R, int V> __host__ __device__ constexpr int cocg_minb() {
+  return sizeof(R) == 8 ? 4 : (V >= 4 ? SLRF_F32_MINB4 : SLRF_F32_MINB);
+}
+// Lane width and row length the kernels can use (else the launchers refuse, code 4).
+template <typename R> inline bool cocg_layout_ok(const CocgArgs<R> &a) {
+  const bool v = sizeof(R) == 8 ? a.vec == 1 : (a.vec == 2 || a.vec == 4);
+  return v && a.W > 0 && a.W % (32 * a.vec) == 0;
+}
 
 // gscale[c] = 1 / max |g[:, c]| (tmp: k words of scratch)
 void col_scale(int64_t n, int k, const double *g, int ld, unsigned long long *tmp, double *gscale, cudaStream_t st);
@@ -154,6 +169,17 @@ template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args,
 void cocg_kernel_attrs();
 // Resident blocks per SM of the grouped SpMM of height G (after cocg_kernel_attrs; 0 on error).
 int grp_blocks_per_sm(int G, bool fp32);
+
+// Real products through the FP32 grouped records (G > 1): YA = A X and/or YB = B X (either
+// output may be null) for a real FP64 block X of k columns, in FP32 products and sums.  X is
+// first copied to x32 in FP32 ([n][grp_real32_ld(k)], padding zero), row i multiplied by
+// xscale[i] (null: 1); output row i is multiplied by yscale[i] (null: 1).  The records'
+// values are those the records were built from (the Jacobi-scaled ones when the
+// preconditioner is on).  nrb row blocks per column tile; *err as for the COCG SpMM.
+int grp_real32_ld(int k);
+void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err,
+                     int nrb, const double *X, int ldx, int k, const double *xscale, float *x32, double *YA,
+                     double *YB, int ldy, const double *yscale, cudaStream_t st);
 
 
 // Grouped-row format: cnt[g] = number of distinct columns of rows [G g, G g + G) (grp_count),

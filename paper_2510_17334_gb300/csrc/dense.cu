@@ -120,8 +120,9 @@ __global__ void __launch_bounds__(256) spmm_b32_kernel(int64_t n, const int64_t 
   }
 }
 
-// YA = A X and YB = B X with FP32 products and sums (FP64 in and out): the real sweep that
-// starts the complex-FP32 solves (q0 = c (A g - sigma B g) only enters FP32 arithmetic).
+// YA = A X and YB = B X with FP32 products and sums (FP64 in and out; either output may be
+// null): the real sweep that starts the complex-FP32 solves (q0 = c (A g - sigma B g) only
+// enters FP32 arithmetic).
 template <int U>
 __global__ void __launch_bounds__(256) spmm_ab32_kernel(int64_t n, const int64_t *__restrict__ rowptr,
                                                         const int32_t *__restrict__ col,
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(256) spmm_ab32_kernel(int64_t n, const int64_t
   for (int u = 0; u < U; ++u) {
     const int cc = c0 + 32 * u;
     if (cc < k) {
-      YA[(size_t)i * ldy + cc] = (double)sa[u];
-      YB[(size_t)i * ldy + cc] = (double)sb[u];
+      if (YA) YA[(size_t)i * ldy + cc] = (double)sa[u];
+      if (YB) YB[(size_t)i * ldy + cc] = (double)sb[u];
     }
   }
 }

@@ -82,6 +82,8 @@ struct slrf_ctx {
   unsigned long long *gmax = nullptr;
   double2 *D64 = nullptr;            // FP32 path with refinement: FP64 correction [n][Wmax]
   double *uacc = nullptr;            // filter accumulator of the updates without refinement [n][Wmax/mp]
+  float *x32 = nullptr;              // FP32 copy of a real block for the grouped real SpMM [n][ld32(L)]
+  double *dsqrt = nullptr;           // D^1/2 (Jacobi preconditioner): unscaled products from scaled records
   double *r00 = nullptr;             // ||r0||^2 of the first refinement step, per w
   int last_k = 0, last_W = 0;
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
@@ -167,6 +169,10 @@ static const double *cocg_valA(const slrf_ctx *c) { return c->dsc ? c->valAs : c
 static const double *cocg_valB(const slrf_ctx *c) { return c->dsc ? c->valBs : c->valB; }
 
 
+__global__ void recip_kernel(int64_t count, const double *a, double *b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) b[i] = 1.0 / a[i];
+}
 __global__ void to_float_kernel(int64_t count, const double *a, float *b) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < count) b[t] = (float)a[t];
@@ -251,6 +257,7 @@ static void drop_groups(slrf_ctx *ctx) {
   ctx->grp = 1;
   ctx->ngroups = 0;
   ctx->grp_bpsm = 0;
+  ctx->vec = ctx->mixed ? cocg_vec_csr<float>() : cocg_vec_csr<double>();
 }
 static int build_groups(slrf_ctx *ctx, int G) {
   drop_groups(ctx);
@@ -273,6 +280,7 @@ static int build_groups(slrf_ctx *ctx, int G) {
   if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
   ctx->grp = G;
   ctx->ngroups = ng;
+  ctx->vec = ctx->mixed ? cocg_vec_grp<float>() : cocg_vec_grp<double>();
   ctx->grp_bpsm = grp_blocks_per_sm(G, ctx->mixed);
   return SLRF_OK;
 }
@@ -330,11 +338,16 @@ static int64_t row_blocks(const slrf_ctx *ctx) {
   const int per_sm = (ctx->grp > 1 && ctx->grp_bpsm > 0) ? std::min(ctx->grp_bpsm, 4) : 4;
   return (int64_t)ctx->sm_count * per_sm;
 }
+// row blocks of the grouped real SpMM: one resident wave, no more than there are stripes
+static int grp_real_blocks(const slrf_ctx *ctx) {
+  const int64_t stripes = (ctx->ngroups + kWarps - 1) / kWarps;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(row_blocks(ctx), stripes));
+}
 
 // COCG arguments of one filter apply of this context (k columns, optional warm start).
 template <typename R>
 static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int k, double *U, int ldu, int &nref) {
-  const int vec = cocg_vec<R>();
+  const int vec = ctx->vec;  // lane width of the SpMM format in use
   const int kp = kpad_of(k, ctx->mp, vec);
   const int W = kp * ctx->mp;
   // row blocks per tile (row_blocks); an autotuned row count (slrf_opts.autotune) replaces it
@@ -361,7 +374,7 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   a.err = ctx->iflags + 15;
   a.dsc = ctx->dsc;
   a.uacc = ctx->uacc;
-  a.W = W; a.k = k; a.m = ctx->m; a.mp = ctx->mp;
+  a.W = W; a.vec = vec; a.k = k; a.m = ctx->m; a.mp = ctx->mp;
   a.rows_per_block = (int)rpb; a.nrb = nrb;
   a.d = (cx_t<R> *)ctx->cd; a.r = (cx_t<R> *)ctx->cr; a.p = (cx_t<R> *)ctx->cp; a.q = (cx_t<R> *)ctx->cq;
   a.partial = ctx->partial; a.counters = ctx->counters; a.ws = ctx->ws;
@@ -404,7 +417,7 @@ static int run_cocg(slrf_ctx *ctx, const double *X, int ldx, int k, const double
   CocgArgs<R> a = build_cocg_args<R>(ctx, X, ldx, k, U, ldu, nref);
   const int W = a.W;
   const int itm = ctx->it_cur > 0 ? ctx->it_cur : ctx->o.it_max;
-  const int T = W / (32 * cocg_vec<R>());  // column tiles
+  const int T = W / (32 * a.vec);  // column tiles
   // Two-group schedule (graph and direct paths, FP32 path): the tiles are split into two
   // groups that run one launch apart, so that each launch carries the SpMM of one group and
   // the update of the other (cocg_dual); each group still alternates update and SpMM in
@@ -526,7 +539,10 @@ static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
     ctx->launches += 1;
   }
   // A g and B g only start the COCG recurrences (q0); in the mixed path those run in FP32
-  if (ctx->mixed)
+  if (ctx->mixed && ctx->grp > 1)  // the records hold exactly the values the solves use
+    spmm_grp_real32(ctx->n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx),
+                    ctx->G, L, k, nullptr, ctx->x32, ctx->AG, ctx->BG, L, nullptr, st);
+  else if (ctx->mixed)
     spmm_ab32(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
   else
     spmm_real(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
@@ -689,7 +705,13 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   double *U1 = ctx->U2, *AU1 = ctx->AG;
   // pass 1: U1 = U R1^{-1}, R1 from the FP32 Gram; if that Gram is not numerically
   // positive definite (kappa(U) beyond ~1e3), iflags[11] triggers the FP64 Gram instead
-  spmm_b32(n, ctx->rowptr, ctx->col, ctx->valB, U, L, k, ctx->BU, L, st);  // FP32 B U: feeds the FP32 Gram
+  // FP32 B U: feeds the FP32 Gram.  Through the FP32 records when there are any; with the
+  // preconditioner they hold D^-1/2 B D^-1/2, so B U = D^1/2 (D^-1/2 B D^-1/2) (D^1/2 U)
+  if (ctx->mixed && ctx->grp > 1)
+    spmm_grp_real32(n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx), U, L,
+                    k, ctx->dsqrt, ctx->x32, nullptr, ctx->BU, L, ctx->dsqrt, st);
+  else
+    spmm_b32(n, ctx->rowptr, ctx->col, ctx->valB, U, L, k, ctx->BU, L, st);
   cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
   tsgram(ctx, n, U, L, k, ctx->BU, L, k, ctx->Gm, k, true, true);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 11, st, nullptr, true);
@@ -780,7 +802,7 @@ template <typename R>
 static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const std::vector<int> &kk,
                               const std::vector<char> &warm, int64_t &launches) {
   slrf_ctx *ctx = nullptr;  // for CK
-  const int vec = cocg_vec<R>();
+  const int vec = cocg_vec_csr<R>();  // the batched kernels run the plain CSR lane width
   CocgArgs<R> *ha = reinterpret_cast<CocgArgs<R> *>(b->hargs);
   int nref = 1, total = 0, itm = 0;
   const int P = (int)act.size();
@@ -793,6 +815,7 @@ static int batch_outer_filter(slrf_batch *b, const std::vector<int> &act, const 
     if (rc != SLRF_OK) return rc;
     ha[i] = build_cocg_args<R>(c, c->V, c->L, k, c->U, c->L, nref);
     ha[i].it_cap = c->o.it_adapt ? c->it_cur : 0;  // per-problem It_max inside the shared loop
+    if (ha[i].vec != vec || ha[i].G != 1) return SLRF_EINVAL;  // the batched setup forces group = 1
     for (int step = 1; step <= nref; ++step) {  // the batched kernels read these buffers unchecked
       int fm_mid, fm_last;
       update_modes<R>(nref, step, fm_mid, fm_last);
@@ -1007,21 +1030,22 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   ctx->m = o.m;
   ctx->mp = pow2_at_least(o.m);
   ctx->mixed = o.precision == 1;
-  ctx->vec = ctx->mixed ? cocg_vec<float>() : cocg_vec<double>();
+  ctx->vec = ctx->mixed ? cocg_vec_csr<float>() : cocg_vec_csr<double>();  // until groups are built
   const int64_t n = ctx->n;
   const int L = block_L;
-  const int kp = kpad_of(L, ctx->mp, ctx->vec);
+  // state sized for the widest lane layout (the grouped SpMM may be chosen below)
+  const int kp = kpad_of(L, ctx->mp, ctx->mixed ? cocg_vec_max<float>() : cocg_vec_max<double>());
   ctx->Wmax = (size_t)kp * ctx->mp;
   // working-set estimate against free memory
   const size_t csz = ctx->mixed ? 8 : 16;
   const size_t state = 4 * (size_t)n * ctx->Wmax * csz;
-  const size_t ntiles_max = ctx->Wmax / (32 * ctx->vec);
+  const size_t ntiles_max = ctx->Wmax / (32 * (ctx->mixed ? cocg_vec_csr<float>() : cocg_vec_csr<double>()));
   // run_cocg uses at most 4 row blocks per SM for any k <= L
   const size_t partial = (size_t)ctx->sm_count * 4 * ctx->Wmax * kNQ;
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
   const size_t refine = (ctx->mixed && o.refine_max > 1) ? 16 * (size_t)n * ctx->Wmax : 0;
-  const size_t uacc = 8 * (size_t)n * (ctx->Wmax / ctx->mp);
+  const size_t uacc = 8 * (size_t)n * (ctx->Wmax / ctx->mp) + (ctx->mixed ? 4 * (size_t)n * grp_real32_ld(L) : 0);
   const size_t need = (state + blocks + matrix + refine + uacc) + 8 * partial + (64u << 20);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(SLRF_ECUDA);
@@ -1129,6 +1153,11 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
     AL(ctx->r00, ctx->Wmax);
   }
   AL(ctx->uacc, (size_t)n * (ctx->Wmax / ctx->mp));
+  if (ctx->mixed) AL(ctx->x32, (size_t)n * grp_real32_ld(L));
+  if (ctx->dsc != nullptr) {
+    AL(ctx->dsqrt, (size_t)n);
+    recip_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->st>>>(n, ctx->dsc, ctx->dsqrt);
+  }
   // real blocks
   const size_t nb = (size_t)n * L;
   AL(ctx->V, nb); AL(ctx->AV, nb); AL(ctx->BV, nb);
@@ -1183,6 +1212,25 @@ int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta
   if (!X || !U || k < 1 || k > ctx->L || X == U) return SLRF_EINVAL;
   StreamScope sc(ctx);
   return filter_impl(ctx, X, k, k, theta, nullptr, nullptr, U, k, false);
+}
+
+int slrf_apply(slrf_ctx *ctx, const double *X, int k, double *AX, double *BX, int fp32) {
+  if (!ctx) return SLRF_EINVAL;
+  if (ctx->status != SLRF_OK) return SLRF_ESTATE;
+  if (!X || k < 1 || k > ctx->L || (!AX && !BX) || X == AX || X == BX || AX == BX) return SLRF_EINVAL;
+  StreamScope sc(ctx);
+  const int64_t n = ctx->n;
+  if (fp32 && ctx->mixed && ctx->grp > 1) {
+    // FP32 records (Jacobi-scaled values when the preconditioner is on: scale both sides by D^1/2)
+    spmm_grp_real32(n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx), X, k,
+                    k, ctx->dsqrt, ctx->x32, AX, BX, k, ctx->dsqrt, ctx->st);
+  } else if (fp32) {
+    spmm_ab32(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, k, k, AX, BX, k, ctx->st);
+  } else {
+    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, k, k, AX, BX, k, ctx->st);
+  }
+  CKL();
+  return SLRF_OK;
 }
 
 int slrf_filter_timing(slrf_ctx *ctx, const double *X, int k, const double *theta, double *U, double *ms,

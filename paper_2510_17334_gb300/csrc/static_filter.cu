@@ -195,6 +195,7 @@ extern "C" int slrf_filter_apply_static(const slrf_csr_pair *pc, double gamma, c
   ca.valA = pc->valA;
   ca.valB = pc->valB;
   ca.W = W;
+  ca.vec = 1;
   ca.k = k;
   ca.m = m;
   ca.mp = mp;

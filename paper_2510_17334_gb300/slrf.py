@@ -32,7 +32,8 @@ SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_app
            "slrf_filter_stats",
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
            "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static", "slrf_setup_batched",
-           "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm", "slrf_wait_selftest")
+           "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm", "slrf_wait_selftest",
+           "slrf_apply")
 
 
 class SlrfError(RuntimeError):
@@ -79,6 +80,7 @@ def lib() -> ct.CDLL:
         L.slrf_setup.argtypes = [ct.POINTER(vp), ct.POINTER(CsrPair), d, i, ct.POINTER(Opts), vp]
         L.slrf_get_poles.argtypes = [vp, ct.POINTER(i), vp, vp]
         L.slrf_filter_apply.argtypes = [vp, vp, i, vp, vp]
+        L.slrf_apply.argtypes = [vp, vp, i, vp, vp, i]
         L.slrf_filter_stats.argtypes = [vp, vp, vp, vp]
         L.slrf_filter_timing.argtypes = [vp, vp, i, vp, vp, vp, vp]
         L.slrf_rayleigh_ritz.argtypes = [vp, vp, i, vp, vp, i, i, vp, vp, vp]
@@ -190,6 +192,15 @@ class Context:
         th = None if theta is None else _dev(theta, torch.float64)
         _check(lib().slrf_filter_apply(self.h, _ptr(X), k, _ptr(th), _ptr(U)), "slrf_filter_apply")
         return U
+
+    def apply(self, X: torch.Tensor, fp32: bool = False, want_a: bool = True, want_b: bool = True):
+        """(A X, B X) with the context's matrices (see slrf_apply); an output not wanted is None."""
+        X = _dev(X, torch.float64)
+        k = X.shape[1]
+        AX = torch.empty_like(X) if want_a else None
+        BX = torch.empty_like(X) if want_b else None
+        _check(lib().slrf_apply(self.h, _ptr(X), k, _ptr(AX), _ptr(BX), 1 if fp32 else 0), "slrf_apply")
+        return AX, BX
 
     def filter_timing(self, X: torch.Tensor, theta: torch.Tensor | None = None):
         """Kernel-by-kernel CUDA-event timing of one filter apply (see slrf_filter_timing)."""
