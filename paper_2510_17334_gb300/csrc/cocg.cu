@@ -53,6 +53,21 @@ namespace slrf {
 // VEC complex entries of one lane (16-byte loads: one in FP64, VEC / 2 in FP32)
 template <typename R, int V> struct Vec { cx_t<R> z[V]; };
 
+// Where the lane's 16-byte pieces live.  The kernels index the complex state (r, p, q, d)
+// logically -- lane l owns the entries [V l, V l + V) of a tile of 32 V -- and reach it only
+// through ldv / stv at tile + V l.  With V > 2 (FP32, two pieces per lane) the pieces are
+// stored 64 entries apart, piece j of lane l at tile + 64 j + 2 l, so that every load
+// instruction of the warp covers 512 contiguous bytes (with the pieces side by side, each
+// instruction would touch every sector of the 1 KB segment and use half of it).
+template <typename R, int V> __device__ __forceinline__ const float4 *piece(const cx_t<R> *p, int j) {
+  const int lane = threadIdx.x & 31;
+  return reinterpret_cast<const float4 *>(p - (V - 2) * lane + 64 * j);
+}
+template <typename R, int V> __device__ __forceinline__ float4 *piece(cx_t<R> *p, int j) {
+  const int lane = threadIdx.x & 31;
+  return reinterpret_cast<float4 *>(p - (V - 2) * lane + 64 * j);
+}
+
 template <typename R, int V> __device__ __forceinline__ Vec<R, V> ldv(const cx_t<R> *p) {
   Vec<R, V> v;
   if constexpr (sizeof(R) == 8) {
@@ -60,7 +75,7 @@ template <typename R, int V> __device__ __forceinline__ Vec<R, V> ldv(const cx_t
   } else {
 #pragma unroll
     for (int j = 0; j < V / 2; ++j) {
-      const float4 t = reinterpret_cast<const float4 *>(p)[j];
+      const float4 t = *piece<R, V>(p, j);
       v.z[2 * j] = make_float2(t.x, t.y);
       v.z[2 * j + 1] = make_float2(t.z, t.w);
     }
@@ -73,7 +88,7 @@ template <typename R, int V> __device__ __forceinline__ void stv(cx_t<R> *p, con
   } else {
 #pragma unroll
     for (int j = 0; j < V / 2; ++j)
-      reinterpret_cast<float4 *>(p)[j] = make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y);
+      *piece<R, V>(p, j) = make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y);
   }
 }
 
@@ -92,7 +107,7 @@ template <typename R, int V> __device__ __forceinline__ Vec<R, V> ldv_cs(const c
     } else {
 #pragma unroll
       for (int j = 0; j < V / 2; ++j) {
-        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p) + j);
+        const float4 t = __ldcs(piece<R, V>(p, j));
         v.z[2 * j] = make_float2(t.x, t.y);
         v.z[2 * j + 1] = make_float2(t.z, t.w);
       }
@@ -108,8 +123,7 @@ template <typename R, int V> __device__ __forceinline__ void stv_cs(cx_t<R> *p, 
   } else {
 #pragma unroll
     for (int j = 0; j < V / 2; ++j)
-      __stcs(reinterpret_cast<float4 *>(p) + j,
-             make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y));
+      __stcs(piece<R, V>(p, j), make_float4(v.z[2 * j].x, v.z[2 * j].y, v.z[2 * j + 1].x, v.z[2 * j + 1].y));
   }
 }
 
@@ -1346,7 +1360,9 @@ __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = (int)blockIdx.y * 64 * VEC + lane * 2 * VEC;  // this lane's first real column
+  const int c0 = (int)blockIdx.y * 64 * VEC + lane * 2 * VEC;  // the lane's pointer (see ldv): tile + 2 VEC lane
+  // pair v of the lane (two real columns) sits at pair index 64 (v / 2) + 2 lane + v % 2 of the tile
+  const int ct = (int)blockIdx.y * 64 * VEC;
   const int64_t gstride = (int64_t)a.nrb * kWarps;
   const int64_t gfirst = (int64_t)blockIdx.x * kWarps + warp;
   if (gfirst >= a.ngroups) return;  // warp-uniform; the kernel has no block-wide barrier
@@ -1360,7 +1376,7 @@ __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>
       for (int v = 0; v < VEC; ++v)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int c = c0 + 2 * v + e;
+          const int c = ct + 2 * (64 * (v / 2) + 2 * lane + (v % 2)) + e;
           if (c < a.k) {
             if (a.YA) a.YA[(size_t)i * a.ldy + c] = ys * (double)(e ? sa[j][v].y : sa[j][v].x);
             if (a.YB) a.YB[(size_t)i * a.ldy + c] = ys * (double)(e ? sb[j][v].y : sb[j][v].x);

@@ -89,7 +89,7 @@ struct CocgArgs {
 // Record size of the grouped-row SpMM: 2 G values of 8 bytes and the column, rounded up to 16.
 template <int G> __host__ __device__ constexpr int grec_bytes() { return (16 * G + 4 + 15) / 16 * 16; }
 #ifndef SLRF_GRP_CHUNK
-#define SLRF_GRP_CHUNK 32
+#define SLRF_GRP_CHUNK 64
 #endif
 constexpr int kGrpChunk = SLRF_GRP_CHUNK;  // records per staged chunk (one bulk copy)
 // Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.

@@ -696,6 +696,185 @@ __global__ void __launch_bounds__(1024) chol_inv_smem_kernel(int k, const double
 
 constexpr size_t kCholSmemMax = 220 * 1024;
 
+// Blocked Cholesky and inverse over many CTAs.  GB300 runs FP64 at 2 FMA/clock/SM, so the
+// k^3/3 + k^3/6 FMAs of one factorisation and inverse need many SMs once k reaches a few
+// hundred (k = 480: 18 ms on one SM).  Panels of kCb columns:
+//   chol_panel_kernel: every CTA factors the diagonal block D = G[j0.., j0..] itself (a
+//     32 x 32 problem in shared memory), then the rows [j1 + 32 blockIdx.x, +32) of the
+//     panel below: L[i][j0 + c] = (G[i][j0 + c] - sum_{l < c} L[i][j0 + l] D[c][l]) / D[c][c];
+//   chol_syrk_kernel: the trailing lower triangle G[i][l] -= sum_c L[i][j0 + c] L[l][j0 + c],
+//     one CTA per 32 x 32 tile (i >= l);
+//   tri_inv_kernel: X = L^{-1} by blocks of kCi columns (one CTA each), rows in blocks of kCi:
+//     X[I][C] = L[I][I]^{-1} (E[I][C] - L[I][<I] X[<I][C]), stored as R^{-1}[c][i] = X[i][c].
+// A pivot that is not positive (or not finite) raises *status (SLRF_ECHOL); every kernel
+// returns at once when *status is already raised or *run_if is zero.
+constexpr int kCb = 32;
+constexpr int kCi = 8;
+#ifndef SLRF_CHOL_BLOCKED_MIN
+#define SLRF_CHOL_BLOCKED_MIN 96
+#endif
+constexpr int kCholBlockedMin = SLRF_CHOL_BLOCKED_MIN;  // smallest k for the blocked kernels
+__device__ __forceinline__ bool chol_skip(const int *status, const int *run_if) {
+  return (run_if != nullptr && *run_if == 0) || *reinterpret_cast<const volatile int *>(status) != 0;
+}
+__global__ void __launch_bounds__(256) chol_panel_kernel(int k, double *G, int ldg, int j0, int *status,
+                                                         const int *run_if) {
+  if (chol_skip(status, run_if)) return;
+  __shared__ double D[kCb][kCb + 1];
+  __shared__ int fail;
+  const int b = min(kCb, k - j0);
+  const int tid = threadIdx.x;
+  if (tid == 0) fail = 0;
+  for (int e = tid; e < kCb * kCb; e += blockDim.x) {
+    const int i = e / kCb, l = e % kCb;
+    D[i][l] = (i < b && l <= i) ? G[(size_t)(j0 + i) * ldg + j0 + l] : 0.0;
+  }
+  __syncthreads();
+  // unblocked right-looking factorisation of D by warp 0 (lane i owns row i)
+  if (tid < 32) {
+    const int i = tid;
+    for (int j = 0; j < b; ++j) {
+      if (i == j) {
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) fail = 1;
+        D[j][j] = (d > 0.0 && isfinite(d)) ? sqrt(d) : 1.0;
+      }
+      __syncwarp();
+      if (i > j && i < b) D[i][j] /= D[j][j];
+      __syncwarp();
+      if (i > j && i < b)
+        for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    if (blockIdx.x == 0 && tid == 0) atomicExch(status, SLRF_ECHOL);
+    return;
+  }
+  if (blockIdx.x == 0)
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int i = e / b, l = e % b;
+      if (l <= i) G[(size_t)(j0 + i) * ldg + j0 + l] = D[i][l];
+    }
+  // panel rows of this CTA: forward substitution with D^T, one row per thread
+  const int j1 = j0 + b;
+  const int r = j1 + (int)blockIdx.x * kCb + tid;
+  if (tid < kCb && r < k) {
+    double x[kCb];
+    double *row = G + (size_t)r * ldg + j0;
+#pragma unroll
+    for (int c = 0; c < kCb; ++c) x[c] = c < b ? row[c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kCb; ++c) {
+      if (c < b) {
+        double v = x[c];
+#pragma unroll
+        for (int l = 0; l < c; ++l) v -= x[l] * D[c][l];
+        x[c] = v / D[c][c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCb; ++c)
+      if (c < b) row[c] = x[c];
+  }
+}
+__global__ void __launch_bounds__(256) chol_syrk_kernel(int k, double *G, int ldg, int j0, int b, int *status,
+                                                        const int *run_if) {
+  if (chol_skip(status, run_if)) return;
+  // tile (ti, tj), ti >= tj, from the linear block index
+  int t = (int)blockIdx.x, ti = 0;
+  while (t > ti) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  const int j1 = j0 + b;
+  const int i0 = j1 + ti * 32, l0 = j1 + tj * 32;
+  __shared__ double Pi[32][kCb + 1], Pl[32][kCb + 1];
+  for (int e = threadIdx.x; e < 32 * kCb; e += blockDim.x) {
+    const int rr = e / kCb, c = e % kCb;
+    Pi[rr][c] = (i0 + rr < k && c < b) ? G[(size_t)(i0 + rr) * ldg + j0 + c] : 0.0;
+    Pl[rr][c] = (l0 + rr < k && c < b) ? G[(size_t)(l0 + rr) * ldg + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  // thread: row i0 + (tid / 8), columns l0 + (tid % 8) + 8 u
+  const int ri = threadIdx.x >> 3, cl = threadIdx.x & 7;
+  const int i = i0 + ri;
+  if (i >= k) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int lc = cl + 8 * u, l = l0 + lc;
+    if (l > i || l >= k) continue;
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < kCb; ++c) s = fma(Pi[ri][c], Pl[lc][c], s);
+    G[(size_t)i * ldg + l] -= s;
+  }
+}
+__global__ void __launch_bounds__(256) tri_inv_kernel(int k, const double *G, int ldg, double *Rinv, int ldr,
+                                                      int *status, const int *run_if) {
+  if (chol_skip(status, run_if)) return;
+  extern __shared__ __align__(16) unsigned char tri_smem[];
+  double *X = reinterpret_cast<double *>(tri_smem);  // [k][kCi]: X[i][cc], column c0 + cc
+  const int c0 = (int)blockIdx.x * kCi;
+  const int tid = threadIdx.x;
+  const int nt = blockDim.x;
+  for (int e = tid; e < k * kCi; e += nt) X[e] = 0.0;
+  __syncthreads();
+  // thread -> (row ri of the row block, column cc); kCi x kCi outputs, split sums over 4 lanes
+  const int cc = tid % kCi, ri = (tid / kCi) % kCi, part = tid / (kCi * kCi);
+  constexpr int kParts = 256 / (kCi * kCi);
+  __shared__ double S[kParts][kCi][kCi];
+  __shared__ double Ld[kCi][kCi + 1];  // the row block's diagonal block of L
+  for (int i0 = c0; i0 < k; i0 += kCi) {
+    const int bi = min(kCi, k - i0);
+    // S = L[I][c0 .. i0) X[c0 .. i0)[C]  (independent loads: several in flight per thread)
+    double s = 0.0;
+    const int i = i0 + ri;
+    if (ri < bi) {
+      const double *gi = G + (size_t)i * ldg;
+#pragma unroll 4
+      for (int l = c0 + part; l < i0; l += kParts) s = fma(gi[l], X[(size_t)l * kCi + cc], s);
+    }
+    S[part][ri][cc] = s;
+    if (tid < kCi * kCi) {
+      const int a = tid / kCi, b = tid % kCi;
+      Ld[a][b] = (a < bi && b <= a) ? G[(size_t)(i0 + a) * ldg + i0 + b] : 0.0;
+    }
+    __syncthreads();
+    // forward substitution inside the block (one thread per column)
+    if (tid < kCi) {
+      const int c = tid, col = c0 + c;
+      for (int rr = 0; rr < bi; ++rr) {
+        const int row = i0 + rr;
+        double v = row == col ? 1.0 : 0.0;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q) v -= S[q][rr][c];
+        for (int l = 0; l < rr; ++l) v -= Ld[rr][l] * X[(size_t)(i0 + l) * kCi + c];
+        X[(size_t)row * kCi + c] = row < col ? 0.0 : v / Ld[rr][rr];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kCi * k; e += nt) {
+    const int c = e / k, i = e % k, col = c0 + c;
+    if (col < k) Rinv[(size_t)col * ldr + i] = i < col ? 0.0 : X[(size_t)i * kCi + c];
+  }
+}
+static void chol_inv_blocked(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st,
+                             const int *run_if) {
+  for (int j0 = 0; j0 < k; j0 += kCb) {
+    const int b = std::min(kCb, k - j0);
+    const int rest = k - j0 - b;
+    const int pb = std::max(1, (rest + kCb - 1) / kCb);
+    chol_panel_kernel<<<pb, 256, 0, st>>>(k, G, ldg, j0, status, run_if);
+    if (rest > 0) {
+      const int T = (rest + 31) / 32;
+      chol_syrk_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(k, G, ldg, j0, b, status, run_if);
+    }
+  }
+  const size_t smem = (size_t)k * kCi * sizeof(double);
+  tri_inv_kernel<<<(k + kCi - 1) / kCi, 256, smem, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
+}
+
 void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cudaStream_t st, const int *run_if,
               bool fp32) {
   static bool attrs = false;
@@ -705,7 +884,14 @@ void chol_inv(int k, double *G, int ldg, double *Rinv, int ldr, int *status, cud
     attrs = true;
   }
   const size_t b64 = ((size_t)k * k + 3 * k) * sizeof(double), b32 = ((size_t)k * k + 3 * k) * sizeof(float);
-  if (fp32 && b32 <= kCholSmemMax)
+  if (k >= kCholBlockedMin && (size_t)k * kCi * sizeof(double) <= kCholSmemMax) {
+    static bool tri_attr = false;
+    if (!tri_attr) {
+      cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax);
+      tri_attr = true;
+    }
+    chol_inv_blocked(k, G, ldg, Rinv, ldr, status, st, run_if);
+  } else if (fp32 && b32 <= kCholSmemMax)
     chol_inv_smem_kernel<float><<<1, 1024, b32, st>>>(k, G, ldg, Rinv, ldr, status, run_if);
   else if (b64 <= kCholSmemMax)
     chol_inv_smem_kernel<double><<<1, 1024, b64, st>>>(k, G, ldg, Rinv, ldr, status, run_if);

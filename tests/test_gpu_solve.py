@@ -66,14 +66,16 @@ def test_rayleigh_ritz_step_parity(slrf_mod, dense):
     ctx.close()
 
 
-@pytest.mark.parametrize("k", [1, 2, 39, 160, 255])
+@pytest.mark.parametrize("k", [1, 2, 39, 97, 160, 255, 480])
 def test_rayleigh_ritz_on_an_invariant_subspace_with_multiplicities(slrf_mod, k):
     """Projected eigenproblem (cooperative Jacobi) on a block that spans k exact eigenvectors
     of the 9^3 Q1 cube Laplacian, whose cube symmetry gives exactly repeated eigenvalues
     (30 triples and 26 sextets among the lowest 255): the Ritz values are the eigenvalues,
     the Ritz vectors satisfy the pencil to rounding level and are B-orthonormal.  Odd k
     exercises the padded index of the round-robin ordering; k = 255 two row entries per
-    thread."""
+    thread.  From k = 96 on the Cholesky factors come from the blocked multi-CTA kernels
+    (97: one column past a panel; 255: ragged last panel and column block; 480: the
+    benched block width)."""
     from slrf_inputs import fem
 
     p = fem.q1_scalar((9, 9, 9), shift=1e-3)
@@ -95,11 +97,12 @@ def test_rayleigh_ritz_on_an_invariant_subspace_with_multiplicities(slrf_mod, k)
     assert np.abs(V.T @ B @ V - np.eye(k)).max() <= 1e-12
 
 
-def test_rayleigh_ritz_reports_a_singular_gram(slrf_mod):
+@pytest.mark.parametrize("k", [4, 128])
+def test_rayleigh_ritz_reports_a_singular_gram(slrf_mod, k):
     n = 200
     p = si.bar1d_pencil(n)
-    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, 100.0, 4, slrf_mod.slrf_opts_default())
-    U = torch.ones(n, 4, dtype=torch.float64)  # rank one
+    ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, 100.0, k, slrf_mod.slrf_opts_default())
+    U = torch.ones(n, k, dtype=torch.float64)  # rank one
     with pytest.raises(slrf_mod.SlrfError) as e:
         ctx.rayleigh_ritz(U)
     assert e.value.status == slrf_mod.SLRF_ECHOL
