@@ -368,6 +368,10 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes of one SpMM launch from an ncu capture of this build (else null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--filter-only", type=int, default=0, metavar="L",
+                    help="profiling aid: kernel-by-kernel timing of filter applies with block L, no JSON line")
+    ap.add_argument("--solve-once", action="store_true",
+                    help="profiling aid: one solve at the bench settings (for launch lists), no JSON line")
     ap.add_argument("--counts-out", default=None,
                     help="write the timed solve's counts (the reference arm's scaling) to this JSON file")
     ap.add_argument("--no-tables", action="store_true",
@@ -445,6 +449,9 @@ def main():
             clk = clocks_stop(cp, cf, local) if clocks else None
             ms = e0.elapsed_time(e1)
         return ctx, V0, found, stats, last, ms, clk
+
+    if args.filter_only or args.solve_once:
+        return profile_aid(args, slrf, si, wl, prec, it_main, precond, stream)
 
     # ---- the timed path
     ctx, V0, found, stats, last, ms, clk = timed_solves(prec, it_main, args.steps, args.warmup, clocks=True)
@@ -535,6 +542,33 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def profile_aid(args, slrf, si, wl, prec, it_main, precond, stream):
+    """Small, self-contained runs to profile under ncu (no JSON line): --filter-only L times
+    3 filter applies of the workload with block L (It_max 4, launch by launch, CUDA events);
+    --solve-once runs one solve at the bench settings."""
+    import torch
+
+    p = wl.pencil
+    L = args.filter_only or wl.block
+    opts = slrf.slrf_opts_default(m=wl.m, it_max=4 if args.filter_only else it_main, precision=prec,
+                                  dense=args.dense, precond=precond, group=args.group)
+    with torch.cuda.stream(stream):
+        ctx = slrf.Context(p.rowptr, p.col, p.valA, p.valB, wl.gamma, L, opts, stream=stream)
+        V0 = torch.from_numpy(si.start_block(p.n, L, wl.seed)).cuda()
+        if args.filter_only:
+            for _ in range(3):
+                tm = ctx.filter_timing(V0)
+            print(f"{args.workload} block {L} precision {prec}: SpMM {tm['ms_spmm'] / max(tm['n_spmm'], 1):.3f} ms, "
+                  f"update {tm['ms_update'] / max(tm['n_update'], 1):.3f} ms, filter {tm['ms_total']:.2f} ms")
+        else:
+            t0 = time.perf_counter()
+            rc, nf, ev, X, rs, st = ctx.solve(V0)
+            torch.cuda.synchronize()
+            print(f"{args.workload} precision {prec}: rc {rc}, {nf} eigenpairs, {time.perf_counter() - t0:.2f} s, "
+                  f"{st['outer_iters']} outer iterations, {st['kernel_launches']} launches")
+        ctx.close()
 
 
 def batch_bench(args, rank, world, local):

@@ -664,7 +664,7 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
                                          const int64_t gfirst, const int64_t gstride, const char *xlane,
                                          const unsigned xbytes, unsigned char *sbuf, uint64_t *bar, Epi &&epi) {
   constexpr int VEC = V;
-  constexpr int RS = grec_bytes<G>();
+  constexpr int RS = grec_bytes<R, G>();
   constexpr int CH = kGrpChunk;
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31;
@@ -730,23 +730,25 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
 #pragma unroll kGrpUnroll
     for (int t = 0; t < cnt; ++t) {
       const unsigned char *rp = rb_ + t * RS;
-      int c = *reinterpret_cast<const int *>(rp + 16 * G);
+      int c = *reinterpret_cast<const int *>(rp + grec_col<R, G>());
       if ((unsigned)c >= (unsigned)nx) {  // a corrupt record: flag it, gather row 0
         atomicCAS(err, 0, 3);
         (void)CHK(21, c, nx);
         c = 0;
       }
       const Vec<R, VEC> x = ldv<R, VEC>(reinterpret_cast<const C *>(xlane + (unsigned long long)(unsigned)c * xbytes));
-      // the record's 2 G values in G 16-byte broadcast loads
-      float4 rv4[G];
+      // the record's 2 G values in 16-byte broadcast loads
+      constexpr int NV = (grec_col<R, G>() + 15) / 16;
+      float4 rv4[NV];
 #pragma unroll
-      for (int j = 0; j < G; ++j) rv4[j] = reinterpret_cast<const float4 *>(rp)[j];
+      for (int j = 0; j < NV; ++j) rv4[j] = reinterpret_cast<const float4 *>(rp)[j];
       const float *rvf = reinterpret_cast<const float *>(rv4);
       if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int j = 0; j < G; ++j) {
-          const float2 av = make_float2(rvf[2 * j], rvf[2 * j + 1]);
-          const float2 bv = make_float2(rvf[2 * (G + j)], rvf[2 * (G + j) + 1]);
+          const float2 av = SLRF_GRP_SPLAT ? make_float2(rvf[2 * j], rvf[2 * j + 1]) : make_float2(rvf[j], rvf[j]);
+          const float2 bv = SLRF_GRP_SPLAT ? make_float2(rvf[2 * (G + j)], rvf[2 * (G + j) + 1])
+                                           : make_float2(rvf[G + j], rvf[G + j]);
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
             sa[j][v] = ffma2(av, x.z[v], sa[j][v]);
@@ -807,7 +809,7 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
 template <typename R, int V, int G, bool FRESH>
 __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr int VEC = V;
-  constexpr int RS = grec_bytes<G>();
+  constexpr int RS = grec_bytes<R, G>();
   using C = cx_t<R>;
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
@@ -1091,7 +1093,7 @@ template <typename R, int G>
 __global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                 const double *__restrict__ valA, const double *__restrict__ valB,
                                 const int64_t *__restrict__ gptr, unsigned char *__restrict__ rec) {
-  constexpr int RS = grec_bytes<G>();
+  constexpr int RS = grec_bytes<R, G>();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i0 = g * G;
   if (i0 >= n) return;
@@ -1109,6 +1111,7 @@ __global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, c
       if (pos[j] < end[j]) { any = true; m = min(m, col[pos[j]]); }
     if (!any) break;
     unsigned char *rp = rec + (size_t)e * RS;
+    for (int t = 0; t < RS / 4; ++t) reinterpret_cast<int *>(rp)[t] = 0;  // padding too
     for (int j = 0; j < G; ++j) {
       double av = 0.0, bv = 0.0;
       if (pos[j] < end[j] && col[pos[j]] == m) {
@@ -1116,15 +1119,18 @@ __global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, c
         bv = valB[pos[j]];
         ++pos[j];
       }
-      if constexpr (sizeof(R) == 4) {
+      if constexpr (sizeof(R) == 4 && SLRF_GRP_SPLAT) {
         reinterpret_cast<float2 *>(rp)[j] = make_float2((float)av, (float)av);
         reinterpret_cast<float2 *>(rp)[G + j] = make_float2((float)bv, (float)bv);
+      } else if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float *>(rp)[j] = (float)av;
+        reinterpret_cast<float *>(rp)[G + j] = (float)bv;
       } else {
         reinterpret_cast<double *>(rp)[j] = av;
         reinterpret_cast<double *>(rp)[G + j] = bv;
       }
     }
-    *reinterpret_cast<int *>(rp + 16 * G) = m;
+    *reinterpret_cast<int *>(rp + grec_col<R, G>()) = m;
     ++e;
   }
 }
@@ -1302,8 +1308,8 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
   with_vec(a, [&](auto vc) { dual_launch<R, decltype(vc)::value>(a, s0, ns, u0, nu, first, fm, st); });
 }
 template <typename R, int V, int G> static void spmm_grp_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
-  if (fresh) cocg_spmm_grp_kernel<R, V, G, true><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
-  else cocg_spmm_grp_kernel<R, V, G, false><<<grid_of(a), kThreads, grp_smem_bytes<G>(), st>>>(a);
+  if (fresh) cocg_spmm_grp_kernel<R, V, G, true><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
+  else cocg_spmm_grp_kernel<R, V, G, false><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
 }
 template <typename R, int V> static void spmm_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   switch (a.G) {
@@ -1356,7 +1362,7 @@ struct GrpReal32 {
 template <int G>
 __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>())) spmm_grp_real32_kernel(const GrpReal32 a) {
   constexpr int VEC = kReal32Vec;
-  constexpr int RS = grec_bytes<G>();
+  constexpr int RS = grec_bytes<float, G>();
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1398,15 +1404,15 @@ void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, con
   GrpReal32 a{n, ngroups, gptr, grec, err, nrb, x32, ld32, k, YA, YB, ldy, yscale};
   const dim3 grid((unsigned)nrb, (unsigned)(ld32 / (64 * kReal32Vec)));
   switch (G) {
-    case 2: spmm_grp_real32_kernel<2><<<grid, kThreads, grp_smem_bytes<2>(), st>>>(a); break;
-    case 3: spmm_grp_real32_kernel<3><<<grid, kThreads, grp_smem_bytes<3>(), st>>>(a); break;
-    case 4: spmm_grp_real32_kernel<4><<<grid, kThreads, grp_smem_bytes<4>(), st>>>(a); break;
+    case 2: spmm_grp_real32_kernel<2><<<grid, kThreads, grp_smem_bytes<float, 2>(), st>>>(a); break;
+    case 3: spmm_grp_real32_kernel<3><<<grid, kThreads, grp_smem_bytes<float, 3>(), st>>>(a); break;
+    case 4: spmm_grp_real32_kernel<4><<<grid, kThreads, grp_smem_bytes<float, 4>(), st>>>(a); break;
     default: break;
   }
 }
 
 template <typename R, int V, int G> static void grp_attrs_v() {
-  const int sm = grp_smem_bytes<G>();
+  const int sm = grp_smem_bytes<R, G>();
   cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
@@ -1416,7 +1422,8 @@ template <typename R, int G> static void grp_attrs() {
   } else {
     grp_attrs_v<R, 2, G>();
     grp_attrs_v<R, 4, G>();
-    cudaFuncSetAttribute(spmm_grp_real32_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, grp_smem_bytes<G>());
+    cudaFuncSetAttribute(spmm_grp_real32_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         grp_smem_bytes<float, G>());
   }
 }
 void cocg_kernel_attrs() {
@@ -1434,7 +1441,7 @@ void cocg_kernel_attrs() {
 template <typename R, int G> static int grp_occ() {
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, cocg_vec_grp<R>(), G, false>, kThreads,
-                                                    grp_smem_bytes<G>()) != cudaSuccess) {
+                                                    grp_smem_bytes<R, G>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -68,9 +68,9 @@ struct CocgArgs {
   double *r00;
   int it_cap;  // > 0: a column stops after this many updates (per-problem It_max in a batch)
   // Grouped-row SpMM (G > 1): rows [G g, G g + G) share one sorted union column list.  Record
-  // e of group g (gptr[g] <= e < gptr[g + 1]) is grec_bytes<G>() bytes: the G rows' A values,
-  // then their B values (FP64: one double each; FP32: each value twice, a float2 pair, the
-  // operand of a packed FP32 FMA), then the column (int32); zero where a row has no entry.
+  // e of group g (gptr[g] <= e < gptr[g + 1]) is grec_bytes<R, G>() bytes: the G rows' A
+  // values, then their B values (one value each in the working precision), then the column
+  // (int32, at grec_col<R, G>()); zero where a row has no entry.
   // The records of a group reach shared memory by 1-D bulk copies (TMA engine).
   int G;                     // rows per group; 1 = plain CSR
   int64_t ngroups;
@@ -86,14 +86,29 @@ struct CocgArgs {
   void *uacc;
 };
 
-// Record size of the grouped-row SpMM: 2 G values of 8 bytes and the column, rounded up to 16.
-template <int G> __host__ __device__ constexpr int grec_bytes() { return (16 * G + 4 + 15) / 16 * 16; }
+// Record of the grouped-row SpMM: 2 G values and the column, rounded up to 16 bytes (G = 3:
+// 64 B in FP64, 32 B in FP32).  SLRF_GRP_SPLAT = 1 stores each FP32 value twice (the (a, a)
+// operand of the packed FMA ready-made, 64 B records); 0 stores it once and pairs it in
+// registers.
+#ifndef SLRF_GRP_SPLAT
+#define SLRF_GRP_SPLAT 0
+#endif
+template <typename R, int G> __host__ __device__ constexpr int grec_col() {
+  return (sizeof(R) == 8 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G;
+}
+template <typename R, int G> __host__ __device__ constexpr int grec_bytes() { return (grec_col<R, G>() + 4 + 15) / 16 * 16; }
+inline int grec_bytes_rt(int G, bool fp32) {
+  const int col = (!fp32 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G;
+  return (col + 4 + 15) / 16 * 16;
+}
 #ifndef SLRF_GRP_CHUNK
 #define SLRF_GRP_CHUNK 64
 #endif
 constexpr int kGrpChunk = SLRF_GRP_CHUNK;  // records per staged chunk (one bulk copy)
 // Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.
-template <int G> __host__ __device__ constexpr int grp_smem_bytes() { return kWarps * 2 * kGrpChunk * grec_bytes<G>(); }
+template <typename R, int G> __host__ __device__ constexpr int grp_smem_bytes() {
+  return kWarps * 2 * kGrpChunk * grec_bytes<R, G>();
+}
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.
 // kAccU: an update of a solve without refinement adds its step to the accumulator (no d

@@ -248,7 +248,7 @@ static int group_counts(slrf_ctx *ctx, int G, std::vector<int> &cnt) {
   cudaFree(d);
   return e == cudaSuccess ? SLRF_OK : SLRF_ECUDA;
 }
-static int grec_size(int G) { return (16 * G + 4 + 15) / 16 * 16; }
+static int grec_size(int G, bool fp32) { return grec_bytes_rt(G, fp32); }
 static void drop_groups(slrf_ctx *ctx) {
   dfree(ctx, ctx->gptr);
   dfree(ctx, ctx->grec);
@@ -269,7 +269,7 @@ static int build_groups(slrf_ctx *ctx, int G) {
   std::vector<int64_t> off((size_t)ng + 1, 0);
   for (int64_t g = 0; g < ng; ++g) off[g + 1] = off[g] + cnt[g];
   if ((rc = dalloc(ctx, &ctx->gptr, (size_t)ng + 1)) != SLRF_OK) return rc;
-  if ((rc = dalloc(ctx, &ctx->grec, (size_t)off[ng] * grec_size(G) + 16)) != SLRF_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->grec, (size_t)off[ng] * grec_size(G, ctx->mixed) + 16)) != SLRF_OK) return rc;
   if (cudaMemcpyAsync(ctx->gptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st) !=
       cudaSuccess)
     return SLRF_ECUDA;
