@@ -6,7 +6,7 @@ Rayleigh-Ritz, residuals, locking and the warm start.  Default workload: the 3D 
 linear-elasticity box on 64 x 64 x 32 nodes (3 dof per node, the z = 0 layer clamped,
 n = 380,928, 29.6M stored entries, lognormal Young's modulus), gamma = 220.8176 (305
 eigenpairs below it), block 480, m = 8 poles, Jacobi-preconditioned inner solves, complex-FP32
-COCG in FP64 refinement (It_max 30); the same solve in FP64 is the "compare" record.  Other
+COCG in FP64 refinement (It_max 25); the same solve in FP64 is the "compare" record.  Other
 workloads (--workload): q1_lap_41 (3D Q1 Laplacian on 41^3 nodes), elast_32 / elast_48,
 bar1d_2000, batch64 (64 uneven pencils solved together), sens48 (48 scaled pencils).
 
@@ -35,10 +35,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DEFAULT_WORKLOAD = "elast_64"
 # It_max of the timed solves per workload (swept on GB300; see the design notes): (mixed, FP64)
-DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 30, "bar1d_2000": 200}
-DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 30, "bar1d_2000": 200}
+# It_max of the timed path (and of the FP64 "compare" record).  64x64x32 box, mixed, GB300:
+# It_max 20 / 25 / 30 / 40 -> 27.1 / 27.9 / 23.5 / 18.2 eigenpairs/s (16 / 12 / 12 / 13 outer steps)
+DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 25, "bar1d_2000": 200}
+DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 25, "bar1d_2000": 200}
 # Jacobi preconditioner on by default for the elasticity boxes (reading R18)
 DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
+# DRAM bytes (read + write) of one full-width launch of the timed path's SpMM kernel, from an
+# ncu capture (profiles/cocg_spmm_grp_f32_elast_64.md: block 32, 2 tiles, scaled to the 30
+# tiles of block 480; traffic is linear in the tiles).  Valid for the kernel as captured.
+DEFAULT_TRAFFIC = {("elast_64", 1): 74.3e9}
 
 
 def measured_hbm_gbs():
@@ -274,7 +280,7 @@ def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic):
     t_alu = flops / (alu_peak * 1e12)
     t_hbm = nbytes / (hbm * 1e9)
     s = spmm_ms / 1e3
-    kern = "cocg_spmm_kernel<double>" if precision == 0 else "cocg_spmm (FP32)"
+    kern = "cocg SpMM, FP64" if precision == 0 else "cocg SpMM, FP32 (grouped-row kernel when the format has groups)"
     if t_alu >= t_hbm:
         achieved = flops / s / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
@@ -463,7 +469,10 @@ def main():
         tim = ctx.filter_timing(V0[:, :wl.block])
     ctx.close()
     spmm_ms = tim["ms_spmm"] / max(tim["n_spmm"], 1)
-    roof = spmm_roofline(p, wl.m, wl.block, prec, spmm_ms, args.traffic_bytes)
+    traffic = args.traffic_bytes
+    if traffic is None and args.group == 0:
+        traffic = DEFAULT_TRAFFIC.get((args.workload, prec))
+    roof = spmm_roofline(p, wl.m, wl.block, prec, spmm_ms, traffic)
     roof["update_ms"] = tim["ms_update"] / max(tim["n_update"], 1)
     roof["spmm_ms"] = spmm_ms
     # ---- the other precision on the same workload (FP64 vs mixed at equal residual)
@@ -624,6 +633,7 @@ def batch_bench(args, rank, world, local):
         return {"value": found / (ms / 1e3), "ms_per_step": ms / args.steps, "rc": rc,
                 "problems_with_exact_count": exact, "eigenpairs": found // args.steps, "max_resid": maxres,
                 "outer_iters_max": st["outer_iters"], "column_iterations": st["column_iterations"],
+                "ms_cocg_per_step": st["ms_filter"], "ms_rest_per_step": st["ms_dense"],
                 "kernel_launches": st["kernel_launches"], "it_max": it_max}, evs
 
     cp, cf = clocks_start(args.clocks_csv)
