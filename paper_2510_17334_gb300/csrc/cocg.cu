@@ -43,6 +43,12 @@
 #ifndef SLRF_GRP_MINB
 #define SLRF_GRP_MINB 2
 #endif
+// Per-record check of the gathered column in the grouped SpMM (1), or none (0): the records
+// are built on the device from a pattern validated at setup and checked once after the
+// build (grp_check), and nothing writes them afterwards (the check costs 5 % of the SpMM).
+#ifndef SLRF_GRP_COLCHECK
+#define SLRF_GRP_COLCHECK 0
+#endif
 namespace slrf {
 constexpr int kGatherUnroll = SLRF_GATHER_UNROLL;  // CSR entries of a row in flight per warp
 constexpr int kGrpUnroll = SLRF_GRP_UNROLL;        // grouped records in flight per warp
@@ -652,7 +658,7 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
 // lane's VEC pairs of the gathered row (x row c at xlane + c * xbytes),
 //   sa[j] += a_j(c) x_c,   sb[j] += b_j(c) x_c      (j < G, the group's rows)
 // over the group's records and then calls epi(g, sa, sb); sa and sb start at zero for every
-// group.  The records go chunk by chunk (kGrpChunk records) through the warp's two shared-
+// group.  The records go chunk by chunk (grp_chunk<R>() records) through the warp's two shared-
 // memory buffers: lane 0 stages the next chunk but one with a 1-D bulk copy, so the records
 // arrive through the TMA engine while the lanes gather and multiply; all lanes read a record
 // with broadcast loads.  FP32: packed FP32 FMAs on (a, a) x (x0, x1).  Waits are bounded
@@ -665,7 +671,7 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
                                          const unsigned xbytes, unsigned char *sbuf, uint64_t *bar, Epi &&epi) {
   constexpr int VEC = V;
   constexpr int RS = grec_bytes<R, G>();
-  constexpr int CH = kGrpChunk;
+  constexpr int CH = grp_chunk<R>();
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31;
   const int64_t gb1 = ngroups;
@@ -731,10 +737,12 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
     for (int t = 0; t < cnt; ++t) {
       const unsigned char *rp = rb_ + t * RS;
       int c = *reinterpret_cast<const int *>(rp + grec_col<R, G>());
-      if ((unsigned)c >= (unsigned)nx) {  // a corrupt record: flag it, gather row 0
-        atomicCAS(err, 0, 3);
-        (void)CHK(21, c, nx);
-        c = 0;
+      if constexpr (SLRF_GRP_COLCHECK != 0) {
+        if ((unsigned)c >= (unsigned)nx) {  // a corrupt record: flag it, gather row 0
+          atomicCAS(err, 0, 3);
+          (void)CHK(21, c, nx);
+          c = 0;
+        }
       }
       const Vec<R, VEC> x = ldv<R, VEC>(reinterpret_cast<const C *>(xlane + (unsigned long long)(unsigned)c * xbytes));
       // the record's 2 G values in 16-byte broadcast loads
@@ -868,7 +876,7 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
     };
     grp_walk<R, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
                    reinterpret_cast<const char *>(a.r + w0), (unsigned)a.W * (unsigned)sizeof(C),
-                   grp_smem + (size_t)warp * 2 * kGrpChunk * RS, s_bar[warp], epi);
+                   grp_smem + (size_t)warp * 2 * grp_chunk<R>() * RS, s_bar[warp], epi);
   }
   spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
@@ -1135,6 +1143,33 @@ __global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, c
   }
 }
 
+// Records of the grouped format: every column in [0, n), offsets non-decreasing from 0.
+// *flag = 1 otherwise.
+template <typename R, int G>
+__global__ void grp_check_kernel(int64_t n, int64_t ngroups, const int64_t *__restrict__ gptr,
+                                 const unsigned char *__restrict__ rec, int *flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nrec = gptr[ngroups];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride)
+    if (gptr[g] < 0 || gptr[g + 1] < gptr[g]) atomicExch(flag, 1);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrec; e += stride) {
+    const int c = *reinterpret_cast<const int *>(rec + (size_t)e * grec_bytes<R, G>() + grec_col<R, G>());
+    if (c < 0 || (int64_t)c >= n) atomicExch(flag, 1);
+  }
+}
+template <typename R>
+void grp_check(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag,
+               int blocks, cudaStream_t st) {
+  switch (G) {
+    case 2: grp_check_kernel<R, 2><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
+    case 3: grp_check_kernel<R, 3><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
+    case 4: grp_check_kernel<R, 4><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
+    default: break;
+  }
+}
+template void grp_check<float>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
+template void grp_check<double>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
+
 void grp_count(int64_t n, int G, const int64_t *rowptr, const int32_t *col, int *cnt, cudaStream_t st) {
   const int64_t ng = (n + G - 1) / G;
   grp_count_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(n, G, rowptr, col, cnt);
@@ -1392,7 +1427,7 @@ __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>
   };
   grp_walk<float, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
                      reinterpret_cast<const char *>(a.x + c0), (unsigned)a.ldx * 4u,
-                     grp_smem + (size_t)warp * 2 * kGrpChunk * RS, s_bar[warp], epi);
+                     grp_smem + (size_t)warp * 2 * grp_chunk<float>() * RS, s_bar[warp], epi);
 }
 void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err,
                      int nrb, const double *X, int ldx, int k, const double *xscale, float *x32, double *YA,

@@ -101,13 +101,17 @@ inline int grec_bytes_rt(int G, bool fp32) {
   const int col = (!fp32 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G;
   return (col + 4 + 15) / 16 * 16;
 }
-#ifndef SLRF_GRP_CHUNK
-#define SLRF_GRP_CHUNK 64
+// Records per staged chunk (one bulk copy): 64 (2 KB of 32-byte FP32 records, 4 KB in FP64).
+#ifndef SLRF_GRP_CHUNK32
+#define SLRF_GRP_CHUNK32 64
 #endif
-constexpr int kGrpChunk = SLRF_GRP_CHUNK;  // records per staged chunk (one bulk copy)
+#ifndef SLRF_GRP_CHUNK64
+#define SLRF_GRP_CHUNK64 64
+#endif
+template <typename R> __host__ __device__ constexpr int grp_chunk() { return sizeof(R) == 4 ? SLRF_GRP_CHUNK32 : SLRF_GRP_CHUNK64; }
 // Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.
 template <typename R, int G> __host__ __device__ constexpr int grp_smem_bytes() {
-  return kWarps * 2 * kGrpChunk * grec_bytes<R, G>();
+  return kWarps * 2 * grp_chunk<R>() * grec_bytes<R, G>();
 }
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.
@@ -182,6 +186,11 @@ template <typename R> void cocg_residual_batched_launch(const CocgArgs<R> *args,
 // Raise the dynamic shared-memory limit of the grouped SpMM kernels (once per process;
 // call before the first launch and outside stream capture).
 void cocg_kernel_attrs();
+// Records of the grouped format checked once after the build (columns in [0, n), offsets
+// non-decreasing); *flag = 1 otherwise.
+template <typename R>
+void grp_check(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag,
+               int blocks, cudaStream_t st);
 // Resident blocks per SM of the grouped SpMM of height G (after cocg_kernel_attrs; 0 on error).
 int grp_blocks_per_sm(int G, bool fp32);
 

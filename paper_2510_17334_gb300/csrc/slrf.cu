@@ -268,7 +268,8 @@ static int build_groups(slrf_ctx *ctx, int G) {
   const int64_t ng = (int64_t)cnt.size();
   std::vector<int64_t> off((size_t)ng + 1, 0);
   for (int64_t g = 0; g < ng; ++g) off[g + 1] = off[g] + cnt[g];
-  if ((rc = dalloc(ctx, &ctx->gptr, (size_t)ng + 1)) != SLRF_OK) return rc;
+  // gptr[ng + 1] (one spare word) holds the record check's flag
+  if ((rc = dalloc(ctx, &ctx->gptr, (size_t)ng + 2)) != SLRF_OK) return rc;
   if ((rc = dalloc(ctx, &ctx->grec, (size_t)off[ng] * grec_size(G, ctx->mixed) + 16)) != SLRF_OK) return rc;
   if (cudaMemcpyAsync(ctx->gptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st) !=
       cudaSuccess)
@@ -277,7 +278,21 @@ static int build_groups(slrf_ctx *ctx, int G) {
     grp_fill<float>(ctx->n, G, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->gptr, ctx->grec, ctx->st);
   else
     grp_fill<double>(ctx->n, G, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->gptr, ctx->grec, ctx->st);
-  if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLRF_ECUDA;
+  // the SpMM trusts the record columns (no per-record check): check every record once
+  int *dflag = reinterpret_cast<int *>(ctx->gptr + ng + 1);
+  int bad = 0;
+  if (cudaMemsetAsync(dflag, 0, sizeof(int), ctx->st) != cudaSuccess) return SLRF_ECUDA;
+  if (ctx->mixed)
+    grp_check<float>(ctx->n, G, ng, ctx->gptr, ctx->grec, dflag, ctx->sm_count * 4, ctx->st);
+  else
+    grp_check<double>(ctx->n, G, ng, ctx->gptr, ctx->grec, dflag, ctx->sm_count * 4, ctx->st);
+  if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return SLRF_ECUDA;
+  if (bad) {
+    drop_groups(ctx);
+    return SLRF_EINVAL;
+  }
   ctx->grp = G;
   ctx->ngroups = ng;
   ctx->vec = ctx->mixed ? cocg_vec_grp<float>() : cocg_vec_grp<double>();

@@ -58,6 +58,9 @@ def test_batched_solve(slrf_mod, precision):
             assert torch.equal(X1, X), i
             ctx.close()
     assert st["n_conv"] == sum(c for _, _, _, c, _ in probs)
+    # the shared COCG launches are timed apart from the per-problem phases
+    assert 0.0 < st["ms_filter"] < st["ms_total"] and st["ms_dense"] > 0.0
+    assert abs(st["ms_filter"] + st["ms_dense"] - st["ms_total"]) <= 1e-6 * st["ms_total"] + 1e-9
     batch.close()
 
 
