@@ -662,8 +662,9 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
 // memory buffers: lane 0 stages the next chunk but one with a 1-D bulk copy, so the records
 // arrive through the TMA engine while the lanes gather and multiply; all lanes read a record
 // with broadcast loads.  FP32: packed FP32 FMAs on (a, a) x (x0, x1).  Waits are bounded
-// (2 s, then *err and a drain of the outstanding copies); a record whose column is out of
-// range sets *err = 3 and gathers row 0, inconsistent offsets set *err = 2.
+// (2 s, then *err and a drain of the outstanding copies); inconsistent offsets set *err = 2
+// (and, with SLRF_GRP_COLCHECK, a record column out of range *err = 3, gathering row 0; by
+// default the columns are checked once when the records are built).
 template <typename R, int V, int G, typename Epi>
 __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *__restrict__ gptr,
                                          const unsigned char *__restrict__ grec, int *err, const int64_t nx,
