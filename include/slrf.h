@@ -94,6 +94,12 @@ typedef struct {
                              all of them): 0 = choose (timed when autotune = 1, else from a
                              cost model of the pattern), 1 = plain CSR, 2..4 = that many;
                              default 0 */
+  int bdiag;              /* 1 = with 3-row groups, use B-diagonal records when the pattern
+                             allows: a vector-valued pencil whose B couples a dof only with the
+                             same dof of a neighbour node (B = M (x) I_3, node-major dofs) keeps
+                             one B value per record and one B product per gathered row instead
+                             of three (checked on the device at setup); 0 = general records;
+                             default 1 */
 } slrf_opts;
 
 /* Statistics of the last slrf_solve (host struct filled by the library). */
@@ -324,6 +330,13 @@ void slrf_destroy(slrf_ctx *ctx);
 
 /* Static description of a status code. */
 const char *slrf_strerror(int status);
+
+/* The COCG SpMM format the context chose at setup (host outputs, any may be NULL): *group =
+ * rows per group (1 = plain CSR), *bdiag = 1 when the grouped records are B-diagonal (see
+ * slrf_opts.bdiag), *lane_width = complex entries per lane of the COCG kernels (FP64 1, FP32 2
+ * or 4).  The paper has no counterpart; it reports the data layout of Sec. 4's inner solves.
+ * Errors: SLRF_EINVAL (NULL ctx). */
+int slrf_format(const slrf_ctx *ctx, int *group, int *bdiag, int *lane_width);
 
 /* First error recorded in the context (SLRF_OK if none). */
 int slrf_last_error(const slrf_ctx *ctx);

@@ -43,6 +43,9 @@
 #ifndef SLRF_GRP_MINB
 #define SLRF_GRP_MINB 2
 #endif
+#ifndef SLRF_GRP_UNROLL_BD
+#define SLRF_GRP_UNROLL_BD 2
+#endif
 // Per-record check of the gathered column in the grouped SpMM (1), or none (0): the records
 // are built on the device from a pattern validated at setup and checked once after the
 // build (grp_check), and nothing writes them afterwards (the check costs 5 % of the SpMM).
@@ -52,6 +55,7 @@
 namespace slrf {
 constexpr int kGatherUnroll = SLRF_GATHER_UNROLL;  // CSR entries of a row in flight per warp
 constexpr int kGrpUnroll = SLRF_GRP_UNROLL;        // grouped records in flight per warp
+constexpr int kGrpUnrollBD = SLRF_GRP_UNROLL_BD;   // node triples in flight per warp (B-diagonal)
 }
 
 namespace slrf {
@@ -665,14 +669,15 @@ __device__ __forceinline__ void cocg_spmm_body(const CocgArgs<R> &a, const int r
 // (2 s, then *err and a drain of the outstanding copies); inconsistent offsets set *err = 2
 // (and, with SLRF_GRP_COLCHECK, a record column out of range *err = 3, gathering row 0; by
 // default the columns are checked once when the records are built).
-template <typename R, int V, int G, typename Epi>
+template <typename R, int V, int G, bool BD, typename Epi>
 __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *__restrict__ gptr,
                                          const unsigned char *__restrict__ grec, int *err, const int64_t nx,
                                          const int64_t gfirst, const int64_t gstride, const char *xlane,
                                          const unsigned xbytes, unsigned char *sbuf, uint64_t *bar, Epi &&epi) {
   constexpr int VEC = V;
-  constexpr int RS = grec_bytes<R, G>();
-  constexpr int CH = grp_chunk<R>();
+  constexpr int RS = grec_bytes<R, G, BD>();
+  constexpr int CH = grp_chunk<R, BD>();
+  static_assert(!BD || (G == 3 && CH % 3 == 0), "B-diagonal records: 3-row groups, whole triples per chunk");
   using C = cx_t<R>;
   const int lane = threadIdx.x & 31;
   const int64_t gb1 = ngroups;
@@ -734,6 +739,45 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
     int cnt;
     first(cg, cc, cnt);
     const unsigned char *rb_ = sbuf + (size_t)b * CH * RS;
+    if constexpr (BD) {
+      // whole node triples: record t + d holds column 3J + d, whose B value belongs to row d
+      // (a malformed tail shorter than a triple is skipped, never read past the chunk)
+#pragma unroll kGrpUnrollBD
+      for (int t = 0; t + 2 < cnt; t += 3) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const unsigned char *rp = rb_ + (t + d) * RS;
+          const int c = *reinterpret_cast<const int *>(rp + grec_col<R, G, true>());
+          const Vec<R, VEC> x = ldv<R, VEC>(reinterpret_cast<const C *>(xlane + (unsigned long long)(unsigned)c * xbytes));
+          if constexpr (sizeof(R) == 4) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(rp);  // a0, a1, a2, b
+            const float2 a0 = make_float2(r4.x, r4.x), a1 = make_float2(r4.y, r4.y), a2 = make_float2(r4.z, r4.z);
+            const float2 bv = make_float2(r4.w, r4.w);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              sa[0][v] = ffma2(a0, x.z[v], sa[0][v]);
+              sa[1][v] = ffma2(a1, x.z[v], sa[1][v]);
+              sa[2][v] = ffma2(a2, x.z[v], sa[2][v]);
+              sb[d][v] = ffma2(bv, x.z[v], sb[d][v]);
+            }
+          } else {
+            const double2 r01 = reinterpret_cast<const double2 *>(rp)[0];  // a0, a1
+            const double2 r23 = reinterpret_cast<const double2 *>(rp)[1];  // a2, b
+            const double av[3] = {r01.x, r01.y, r23.x};
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                sa[j][v].x = fma(av[j], x.z[v].x, sa[j][v].x);
+                sa[j][v].y = fma(av[j], x.z[v].y, sa[j][v].y);
+              }
+              sb[d][v].x = fma(r23.y, x.z[v].x, sb[d][v].x);
+              sb[d][v].y = fma(r23.y, x.z[v].y, sb[d][v].y);
+            }
+          }
+        }
+      }
+    } else {
 #pragma unroll kGrpUnroll
     for (int t = 0; t < cnt; ++t) {
       const unsigned char *rp = rb_ + t * RS;
@@ -780,6 +824,7 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
         }
       }
     }
+    }
     if (cc + 1 >= nchunks(cg)) {
       epi(cg, sa, sb);  // the group's last chunk
 #pragma unroll
@@ -815,10 +860,10 @@ __device__ __forceinline__ void grp_walk(const int64_t ngroups, const int64_t *_
 // (grouped-row format): every gathered row of r feeds all G rows, so a row costs union/G
 // gathers instead of its own count (a 3-dof elasticity node: 27 instead of 81).  Then, per
 // row, p = r + beta p, q = s + beta q and the mu partials.
-template <typename R, int V, int G, bool FRESH>
+template <typename R, int V, int G, bool BD, bool FRESH>
 __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const int rb, const int tile) {
   constexpr int VEC = V;
-  constexpr int RS = grec_bytes<R, G>();
+  constexpr int RS = grec_bytes<R, G, BD>();
   using C = cx_t<R>;
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
@@ -875,9 +920,9 @@ __device__ __forceinline__ void cocg_spmm_grp_body(const CocgArgs<R> &a, const i
         }
       }
     };
-    grp_walk<R, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
-                   reinterpret_cast<const char *>(a.r + w0), (unsigned)a.W * (unsigned)sizeof(C),
-                   grp_smem + (size_t)warp * 2 * grp_chunk<R>() * RS, s_bar[warp], epi);
+    grp_walk<R, VEC, G, BD>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
+                            reinterpret_cast<const char *>(a.r + w0), (unsigned)a.W * (unsigned)sizeof(C),
+                            grp_smem + (size_t)warp * 2 * grp_chunk<R, BD>() * RS, s_bar[warp], epi);
   }
   spmm_tail<R, VEC>(a, acc, w_tile0, rb, tile, a.nrb);
 }
@@ -1023,9 +1068,9 @@ template <typename R, int V, bool FRESH>
 __global__ void __launch_bounds__(kThreads, (cocg_minb<R, V>())) cocg_spmm_kernel(const CocgArgs<R> a) {
   cocg_spmm_body<R, V, FRESH>(a, blockIdx.x, blockIdx.y);
 }
-template <typename R, int V, int G, bool FRESH>
+template <typename R, int V, int G, bool BD, bool FRESH>
 __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<R, V, G>())) cocg_spmm_grp_kernel(const CocgArgs<R> a) {
-  cocg_spmm_grp_body<R, V, G, FRESH>(a, blockIdx.x, blockIdx.y);
+  cocg_spmm_grp_body<R, V, G, BD, FRESH>(a, blockIdx.x, blockIdx.y);
 }
 template <typename R, int V>
 __global__ void __launch_bounds__(kThreads, 2) cocg_residual_kernel(const CocgArgs<R> a) {
@@ -1146,30 +1191,97 @@ __global__ void grp_fill_kernel(int64_t n, const int64_t *__restrict__ rowptr, c
 
 // Records of the grouped format: every column in [0, n), offsets non-decreasing from 0.
 // *flag = 1 otherwise.
-template <typename R, int G>
+template <typename R, int G, bool BD>
 __global__ void grp_check_kernel(int64_t n, int64_t ngroups, const int64_t *__restrict__ gptr,
                                  const unsigned char *__restrict__ rec, int *flag) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nrec = gptr[ngroups];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride)
-    if (gptr[g] < 0 || gptr[g + 1] < gptr[g]) atomicExch(flag, 1);
+    if (gptr[g] < 0 || gptr[g + 1] < gptr[g] || (BD && (gptr[g + 1] - gptr[g]) % 3 != 0)) atomicExch(flag, 1);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrec; e += stride) {
-    const int c = *reinterpret_cast<const int *>(rec + (size_t)e * grec_bytes<R, G>() + grec_col<R, G>());
+    const int c = *reinterpret_cast<const int *>(rec + (size_t)e * grec_bytes<R, G, BD>() + grec_col<R, G, BD>());
     if (c < 0 || (int64_t)c >= n) atomicExch(flag, 1);
   }
 }
 template <typename R>
 void grp_check(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag,
-               int blocks, cudaStream_t st) {
+               int blocks, cudaStream_t st, bool bd) {
   switch (G) {
-    case 2: grp_check_kernel<R, 2><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
-    case 3: grp_check_kernel<R, 3><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
-    case 4: grp_check_kernel<R, 4><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
+    case 2: grp_check_kernel<R, 2, false><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
+    case 3:
+      if (bd) grp_check_kernel<R, 3, true><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag);
+      else grp_check_kernel<R, 3, false><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag);
+      break;
+    case 4: grp_check_kernel<R, 4, false><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag); break;
     default: break;
   }
 }
-template void grp_check<float>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
-template void grp_check<double>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
+template void grp_check<float>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t,
+                               bool);
+template void grp_check<double>(int64_t, int, int64_t, const int64_t *, const unsigned char *, int *, int,
+                                cudaStream_t, bool);
+
+// B-diagonal records: every group of 3 rows (rows 3g .. 3g + 2, node g) has its records in
+// aligned column triples (position t holds column 3J + t mod 3, positions t, t + 1, t + 2 of a
+// triple the same J), and every B value off the row c mod 3 is zero.  One thread per group.
+template <typename R>
+__global__ void grp_bd_detect_kernel(int64_t n, int64_t ngroups, const int64_t *__restrict__ gptr,
+                                     const unsigned char *__restrict__ rec, int *flag) {
+  constexpr int RS = grec_bytes<R, 3>();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    const int64_t e0 = gptr[g], e1 = gptr[g + 1];
+    bool ok = (e1 - e0) % 3 == 0 && 3 * g + 2 < n;
+    for (int64_t e = e0; ok && e < e1; ++e) {
+      const unsigned char *rp = rec + (size_t)e * RS;
+      const int c = *reinterpret_cast<const int *>(rp + grec_col<R, 3>());
+      const int t = (int)((e - e0) % 3);
+      if (c % 3 != t) ok = false;
+      if (t > 0 && c != *reinterpret_cast<const int *>(rp - RS + grec_col<R, 3>()) + 1) ok = false;
+      for (int j = 0; j < 3; ++j) {
+        const double b = sizeof(R) == 8 ? reinterpret_cast<const double *>(rp)[3 + j]
+                                        : (double)reinterpret_cast<const float *>(rp)[SLRF_GRP_SPLAT ? 2 * (3 + j) : 3 + j];
+        if (j != t && b != 0.0) ok = false;
+      }
+    }
+    if (!ok) atomicExch(flag, 1);
+  }
+}
+template <typename R>
+__global__ void grp_bd_convert_kernel(int64_t nrec, const unsigned char *__restrict__ rec, unsigned char *bdrec) {
+  constexpr int RS = grec_bytes<R, 3>(), RB = grec_bytes<R, 3, true>();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrec) return;
+  const unsigned char *rp = rec + (size_t)e * RS;
+  unsigned char *bp = bdrec + (size_t)e * RB;
+  const int c = *reinterpret_cast<const int *>(rp + grec_col<R, 3>());
+  const int d = c % 3;
+  for (int t = 0; t < RB / 4; ++t) reinterpret_cast<int *>(bp)[t] = 0;
+  if constexpr (sizeof(R) == 8) {
+    const double *v = reinterpret_cast<const double *>(rp);
+    double *o = reinterpret_cast<double *>(bp);
+    o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3 + d];
+  } else {
+    const float *v = reinterpret_cast<const float *>(rp);
+    float *o = reinterpret_cast<float *>(bp);
+    const int s = SLRF_GRP_SPLAT ? 2 : 1;
+    o[0] = v[0]; o[1] = v[s]; o[2] = v[2 * s]; o[3] = v[s * (3 + d)];
+  }
+  *reinterpret_cast<int *>(bp + grec_col<R, 3, true>()) = c;
+}
+template <typename R>
+void grp_bd_detect(int64_t n, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag, int blocks,
+                   cudaStream_t st) {
+  grp_bd_detect_kernel<R><<<blocks, 256, 0, st>>>(n, ngroups, gptr, rec, flag);
+}
+template <typename R>
+void grp_bd_convert(int64_t nrec, const unsigned char *rec, unsigned char *bdrec, cudaStream_t st) {
+  if (nrec > 0) grp_bd_convert_kernel<R><<<(unsigned)((nrec + 255) / 256), 256, 0, st>>>(nrec, rec, bdrec);
+}
+template void grp_bd_detect<float>(int64_t, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
+template void grp_bd_detect<double>(int64_t, int64_t, const int64_t *, const unsigned char *, int *, int, cudaStream_t);
+template void grp_bd_convert<float>(int64_t, const unsigned char *, unsigned char *, cudaStream_t);
+template void grp_bd_convert<double>(int64_t, const unsigned char *, unsigned char *, cudaStream_t);
 
 void grp_count(int64_t n, int G, const int64_t *rowptr, const int32_t *col, int *cnt, cudaStream_t st) {
   const int64_t ng = (n + G - 1) / G;
@@ -1344,8 +1456,16 @@ template <typename R> void cocg_dual(const CocgArgs<R> &a, int s0, int ns, int u
   with_vec(a, [&](auto vc) { dual_launch<R, decltype(vc)::value>(a, s0, ns, u0, nu, first, fm, st); });
 }
 template <typename R, int V, int G> static void spmm_grp_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
-  if (fresh) cocg_spmm_grp_kernel<R, V, G, true><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
-  else cocg_spmm_grp_kernel<R, V, G, false><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
+  if constexpr (G == 3) {
+    if (a.bdiag) {
+      constexpr int sm = grp_smem_bytes<R, 3, true>();
+      if (fresh) cocg_spmm_grp_kernel<R, V, 3, true, true><<<grid_of(a), kThreads, sm, st>>>(a);
+      else cocg_spmm_grp_kernel<R, V, 3, true, false><<<grid_of(a), kThreads, sm, st>>>(a);
+      return;
+    }
+  }
+  if (fresh) cocg_spmm_grp_kernel<R, V, G, false, true><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
+  else cocg_spmm_grp_kernel<R, V, G, false, false><<<grid_of(a), kThreads, grp_smem_bytes<R, G>(), st>>>(a);
 }
 template <typename R, int V> static void spmm_launch(const CocgArgs<R> &a, cudaStream_t st, bool fresh) {
   switch (a.G) {
@@ -1395,10 +1515,10 @@ struct GrpReal32 {
   int ldy;
   const double *yscale;
 };
-template <int G>
+template <int G, bool BD>
 __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>())) spmm_grp_real32_kernel(const GrpReal32 a) {
   constexpr int VEC = kReal32Vec;
-  constexpr int RS = grec_bytes<float, G>();
+  constexpr int RS = grec_bytes<float, G, BD>();
   extern __shared__ __align__(128) unsigned char grp_smem[];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1426,13 +1546,13 @@ __global__ void __launch_bounds__(kThreads, (cocg_grp_minb<float, kReal32Vec, G>
         }
     }
   };
-  grp_walk<float, VEC, G>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
-                     reinterpret_cast<const char *>(a.x + c0), (unsigned)a.ldx * 4u,
-                     grp_smem + (size_t)warp * 2 * grp_chunk<float>() * RS, s_bar[warp], epi);
+  grp_walk<float, VEC, G, BD>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
+                              reinterpret_cast<const char *>(a.x + c0), (unsigned)a.ldx * 4u,
+                              grp_smem + (size_t)warp * 2 * grp_chunk<float, BD>() * RS, s_bar[warp], epi);
 }
 void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err,
                      int nrb, const double *X, int ldx, int k, const double *xscale, float *x32, double *YA,
-                     double *YB, int ldy, const double *yscale, cudaStream_t st) {
+                     double *YB, int ldy, const double *yscale, cudaStream_t st, bool bd) {
   if (n <= 0 || k <= 0 || nrb <= 0) return;
   const int ld32 = grp_real32_ld(k);
   const int64_t tot = n * ld32;
@@ -1440,17 +1560,25 @@ void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, con
   GrpReal32 a{n, ngroups, gptr, grec, err, nrb, x32, ld32, k, YA, YB, ldy, yscale};
   const dim3 grid((unsigned)nrb, (unsigned)(ld32 / (64 * kReal32Vec)));
   switch (G) {
-    case 2: spmm_grp_real32_kernel<2><<<grid, kThreads, grp_smem_bytes<float, 2>(), st>>>(a); break;
-    case 3: spmm_grp_real32_kernel<3><<<grid, kThreads, grp_smem_bytes<float, 3>(), st>>>(a); break;
-    case 4: spmm_grp_real32_kernel<4><<<grid, kThreads, grp_smem_bytes<float, 4>(), st>>>(a); break;
+    case 2: spmm_grp_real32_kernel<2, false><<<grid, kThreads, grp_smem_bytes<float, 2>(), st>>>(a); break;
+    case 3:
+      if (bd) spmm_grp_real32_kernel<3, true><<<grid, kThreads, grp_smem_bytes<float, 3, true>(), st>>>(a);
+      else spmm_grp_real32_kernel<3, false><<<grid, kThreads, grp_smem_bytes<float, 3>(), st>>>(a);
+      break;
+    case 4: spmm_grp_real32_kernel<4, false><<<grid, kThreads, grp_smem_bytes<float, 4>(), st>>>(a); break;
     default: break;
   }
 }
 
 template <typename R, int V, int G> static void grp_attrs_v() {
   const int sm = grp_smem_bytes<R, G>();
-  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (G == 3) {
+    const int sbd = grp_smem_bytes<R, 3, true>();
+    cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, 3, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbd);
+    cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, 3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbd);
+  }
 }
 template <typename R, int G> static void grp_attrs() {
   if constexpr (sizeof(R) == 8) {
@@ -1458,8 +1586,11 @@ template <typename R, int G> static void grp_attrs() {
   } else {
     grp_attrs_v<R, 2, G>();
     grp_attrs_v<R, 4, G>();
-    cudaFuncSetAttribute(spmm_grp_real32_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(spmm_grp_real32_kernel<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          grp_smem_bytes<float, G>());
+    if constexpr (G == 3)
+      cudaFuncSetAttribute(spmm_grp_real32_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           grp_smem_bytes<float, 3, true>());
   }
 }
 void cocg_kernel_attrs() {
@@ -1474,20 +1605,22 @@ void cocg_kernel_attrs() {
   cudaGetLastError();
   done = true;
 }
-template <typename R, int G> static int grp_occ() {
+template <typename R, int G, bool BD> static int grp_occ() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, cocg_vec_grp<R>(), G, false>, kThreads,
-                                                    grp_smem_bytes<R, G>()) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cocg_spmm_grp_kernel<R, cocg_vec_grp<R>(), G, BD, false>,
+                                                    kThreads, grp_smem_bytes<R, G, BD>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return b;
 }
-int grp_blocks_per_sm(int G, bool fp32) {
+int grp_blocks_per_sm(int G, bool fp32, bool bd) {
   switch (G) {
-    case 2: return fp32 ? grp_occ<float, 2>() : grp_occ<double, 2>();
-    case 3: return fp32 ? grp_occ<float, 3>() : grp_occ<double, 3>();
-    case 4: return fp32 ? grp_occ<float, 4>() : grp_occ<double, 4>();
+    case 2: return fp32 ? grp_occ<float, 2, false>() : grp_occ<double, 2, false>();
+    case 3:
+      if (bd) return fp32 ? grp_occ<float, 3, true>() : grp_occ<double, 3, true>();
+      return fp32 ? grp_occ<float, 3, false>() : grp_occ<double, 3, false>();
+    case 4: return fp32 ? grp_occ<float, 4, false>() : grp_occ<double, 4, false>();
     default: return 0;
   }
 }

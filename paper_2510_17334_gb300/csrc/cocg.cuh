@@ -76,6 +76,7 @@ struct CocgArgs {
   int64_t ngroups;
   const int64_t *gptr;       // [ngroups + 1]
   const unsigned char *grec; // records, 16-byte aligned
+  int bdiag;                 // 1: B-diagonal records (G = 3, see grec_col)
   int *err;                  // 1: a bounded wait gave up (SLRF_ETIMEOUT); 2, 3: group records
                              // inconsistent; 4: update buffers missing (SLRF_EINVAL)
   // Jacobi preconditioner D = diag(A): the value arrays above are those of
@@ -93,12 +94,22 @@ struct CocgArgs {
 #ifndef SLRF_GRP_SPLAT
 #define SLRF_GRP_SPLAT 0
 #endif
-template <typename R, int G> __host__ __device__ constexpr int grec_col() {
-  return (sizeof(R) == 8 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G;
+//
+// B-diagonal records (BD, 3-row groups only): vector-valued FEM pencils whose B couples a dof
+// only with the same dof of a neighbour node (a mass matrix M (x) I_3) have, in a node's group,
+// one nonzero B value per column c -- the row c mod 3.  When every group's columns come in
+// aligned node triples (3J, 3J + 1, 3J + 2), a record holds the 3 A values, that one B value
+// and the column (FP32 32 B, FP64 48 B), and the walk knows the B row from the record's place
+// in its triple: one B product per record instead of three.  Checked on the device when the
+// records are built (grp_bd_detect); otherwise the general records are kept.
+template <typename R, int G, bool BD = false> __host__ __device__ constexpr int grec_col() {
+  return BD ? 4 * (int)sizeof(R) : ((sizeof(R) == 8 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G);
 }
-template <typename R, int G> __host__ __device__ constexpr int grec_bytes() { return (grec_col<R, G>() + 4 + 15) / 16 * 16; }
-inline int grec_bytes_rt(int G, bool fp32) {
-  const int col = (!fp32 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G;
+template <typename R, int G, bool BD = false> __host__ __device__ constexpr int grec_bytes() {
+  return (grec_col<R, G, BD>() + 4 + 15) / 16 * 16;
+}
+inline int grec_bytes_rt(int G, bool fp32, bool bd = false) {
+  const int col = bd ? (fp32 ? 16 : 32) : ((!fp32 || SLRF_GRP_SPLAT) ? 16 * G : 8 * G);
   return (col + 4 + 15) / 16 * 16;
 }
 // Records per staged chunk (one bulk copy): 64 (2 KB of 32-byte FP32 records, 4 KB in FP64).
@@ -108,10 +119,13 @@ inline int grec_bytes_rt(int G, bool fp32) {
 #ifndef SLRF_GRP_CHUNK64
 #define SLRF_GRP_CHUNK64 64
 #endif
-template <typename R> __host__ __device__ constexpr int grp_chunk() { return sizeof(R) == 4 ? SLRF_GRP_CHUNK32 : SLRF_GRP_CHUNK64; }
+// (B-diagonal records: 63, whole node triples)
+template <typename R, bool BD = false> __host__ __device__ constexpr int grp_chunk() {
+  return BD ? 63 : (sizeof(R) == 4 ? SLRF_GRP_CHUNK32 : SLRF_GRP_CHUNK64);
+}
 // Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.
-template <typename R, int G> __host__ __device__ constexpr int grp_smem_bytes() {
-  return kWarps * 2 * grp_chunk<R>() * grec_bytes<R, G>();
+template <typename R, int G, bool BD = false> __host__ __device__ constexpr int grp_smem_bytes() {
+  return kWarps * 2 * grp_chunk<R, BD>() * grec_bytes<R, G, BD>();
 }
 
 // Final-update modes: how the last COCG update of a solve delivers its correction.
@@ -190,9 +204,17 @@ void cocg_kernel_attrs();
 // non-decreasing); *flag = 1 otherwise.
 template <typename R>
 void grp_check(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag,
-               int blocks, cudaStream_t st);
+               int blocks, cudaStream_t st, bool bd = false);
+// B-diagonal records (see grec_col): *flag = 1 unless every group of 3 rows has its records
+// in aligned column triples and B vanishes off the row c mod 3 (general records as input).
+template <typename R>
+void grp_bd_detect(int64_t n, int64_t ngroups, const int64_t *gptr, const unsigned char *rec, int *flag, int blocks,
+                   cudaStream_t st);
+// General records -> B-diagonal records (nrec of them).
+template <typename R>
+void grp_bd_convert(int64_t nrec, const unsigned char *rec, unsigned char *bdrec, cudaStream_t st);
 // Resident blocks per SM of the grouped SpMM of height G (after cocg_kernel_attrs; 0 on error).
-int grp_blocks_per_sm(int G, bool fp32);
+int grp_blocks_per_sm(int G, bool fp32, bool bd = false);
 
 // Real products through the FP32 grouped records (G > 1): YA = A X and/or YB = B X (either
 // output may be null) for a real FP64 block X of k columns, in FP32 products and sums.  X is
@@ -203,7 +225,7 @@ int grp_blocks_per_sm(int G, bool fp32);
 int grp_real32_ld(int k);
 void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err,
                      int nrb, const double *X, int ldx, int k, const double *xscale, float *x32, double *YA,
-                     double *YB, int ldy, const double *yscale, cudaStream_t st);
+                     double *YB, int ldy, const double *yscale, cudaStream_t st, bool bd = false);
 
 
 // Grouped-row format: cnt[g] = number of distinct columns of rows [G g, G g + G) (grp_count),

@@ -89,6 +89,7 @@ struct slrf_ctx {
   int64_t launches = 0;              // kernels enqueued by the orchestration (statistics)
   int64_t rpb_tuned = 0;             // autotuned COCG rows per block (0 = default)
   int grp_bpsm = 0;                  // resident blocks per SM of the grouped SpMM in use
+  int bdiag = 0;                     // the grouped records are B-diagonal (see grec_col)
   // real n x L blocks (ld = L)
   double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
   double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
@@ -257,6 +258,7 @@ static void drop_groups(slrf_ctx *ctx) {
   ctx->grp = 1;
   ctx->ngroups = 0;
   ctx->grp_bpsm = 0;
+  ctx->bdiag = 0;
   ctx->vec = ctx->mixed ? cocg_vec_csr<float>() : cocg_vec_csr<double>();
 }
 static int build_groups(slrf_ctx *ctx, int G) {
@@ -293,10 +295,44 @@ static int build_groups(slrf_ctx *ctx, int G) {
     drop_groups(ctx);
     return SLRF_EINVAL;
   }
+  // 3-row groups of a vector-valued pencil whose B couples only equal dofs: B-diagonal records
+  int bd = 0;
+  if (G == 3 && ctx->o.bdiag) {
+    int nbd = 0;
+    if (cudaMemsetAsync(dflag, 0, sizeof(int), ctx->st) != cudaSuccess) return SLRF_ECUDA;
+    if (ctx->mixed)
+      grp_bd_detect<float>(ctx->n, ng, ctx->gptr, ctx->grec, dflag, ctx->sm_count * 4, ctx->st);
+    else
+      grp_bd_detect<double>(ctx->n, ng, ctx->gptr, ctx->grec, dflag, ctx->sm_count * 4, ctx->st);
+    if (cudaMemcpyAsync(&nbd, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      return SLRF_ECUDA;
+    if (nbd == 0) {
+      unsigned char *bdrec = nullptr;
+      if ((rc = dalloc(ctx, &bdrec, (size_t)off[ng] * grec_bytes_rt(3, ctx->mixed, true) + 16)) != SLRF_OK) return rc;
+      if (ctx->mixed) grp_bd_convert<float>(off[ng], ctx->grec, bdrec, ctx->st);
+      else grp_bd_convert<double>(off[ng], ctx->grec, bdrec, ctx->st);
+      if (cudaMemsetAsync(dflag, 0, sizeof(int), ctx->st) != cudaSuccess) return SLRF_ECUDA;
+      if (ctx->mixed) grp_check<float>(ctx->n, 3, ng, ctx->gptr, bdrec, dflag, ctx->sm_count * 4, ctx->st, true);
+      else grp_check<double>(ctx->n, 3, ng, ctx->gptr, bdrec, dflag, ctx->sm_count * 4, ctx->st, true);
+      if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+          cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return SLRF_ECUDA;
+      if (bad) {
+        dfree(ctx, bdrec);
+        drop_groups(ctx);
+        return SLRF_EINVAL;
+      }
+      dfree(ctx, ctx->grec);
+      ctx->grec = bdrec;
+      bd = 1;
+    }
+  }
+  ctx->bdiag = bd;
   ctx->grp = G;
   ctx->ngroups = ng;
   ctx->vec = ctx->mixed ? cocg_vec_grp<float>() : cocg_vec_grp<double>();
-  ctx->grp_bpsm = grp_blocks_per_sm(G, ctx->mixed);
+  ctx->grp_bpsm = grp_blocks_per_sm(G, ctx->mixed, bd != 0);
   return SLRF_OK;
 }
 // Candidate G from the pattern.  FP64: the SpMM is bound by the FP64 pipe, so only groups
@@ -386,6 +422,7 @@ static CocgArgs<R> build_cocg_args(slrf_ctx *ctx, const double *X, int ldx, int 
   a.ngroups = ctx->ngroups;
   a.gptr = ctx->gptr;
   a.grec = ctx->grec;
+  a.bdiag = ctx->bdiag;
   a.err = ctx->iflags + 15;
   a.dsc = ctx->dsc;
   a.uacc = ctx->uacc;
@@ -556,7 +593,7 @@ static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
   // A g and B g only start the COCG recurrences (q0); in the mixed path those run in FP32
   if (ctx->mixed && ctx->grp > 1)  // the records hold exactly the values the solves use
     spmm_grp_real32(ctx->n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx),
-                    ctx->G, L, k, nullptr, ctx->x32, ctx->AG, ctx->BG, L, nullptr, st);
+                    ctx->G, L, k, nullptr, ctx->x32, ctx->AG, ctx->BG, L, nullptr, st, ctx->bdiag != 0);
   else if (ctx->mixed)
     spmm_ab32(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
   else
@@ -724,7 +761,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   // preconditioner they hold D^-1/2 B D^-1/2, so B U = D^1/2 (D^-1/2 B D^-1/2) (D^1/2 U)
   if (ctx->mixed && ctx->grp > 1)
     spmm_grp_real32(n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx), U, L,
-                    k, ctx->dsqrt, ctx->x32, nullptr, ctx->BU, L, ctx->dsqrt, st);
+                    k, ctx->dsqrt, ctx->x32, nullptr, ctx->BU, L, ctx->dsqrt, st, ctx->bdiag != 0);
   else
     spmm_b32(n, ctx->rowptr, ctx->col, ctx->valB, U, L, k, ctx->BU, L, st);
   cudaMemsetAsync(ctx->iflags + 11, 0, sizeof(int), st);
@@ -897,6 +934,7 @@ int slrf_opts_default(slrf_opts *o) {
   o->nev = 0;
   o->seed = 1;
   o->dense = 1;
+  o->bdiag = 1;
   return SLRF_OK;
 }
 
@@ -1016,7 +1054,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   if (opts) o = *opts;
   else slrf_opts_default(&o);
   if (o.m < 1 || o.m > 32 || o.it_max < 1 || o.outer_max < 1 || o.refine_max < 1 || o.dense < 0 || o.dense > 1 ||
-      o.it_adapt < 0 || o.it_adapt > 1 || o.precond < 0 || o.precond > 1 || o.group < 0 || o.group > 4)
+      o.it_adapt < 0 || o.it_adapt > 1 || o.precond < 0 || o.precond > 1 || o.group < 0 || o.group > 4 || o.bdiag < 0 ||
+      o.bdiag > 1)
     return SLRF_EINVAL;
   if (block_L > 510) return SLRF_EINVAL;  // the projected eigensolver holds two rows of <= 512 in shared memory
   if (!(o.tol_inner >= 0) || !(o.tol_eig > 0)) return SLRF_EINVAL;
@@ -1232,6 +1271,14 @@ int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta
   return filter_impl(ctx, X, k, k, theta, nullptr, nullptr, U, k, false);
 }
 
+int slrf_format(const slrf_ctx *ctx, int *group, int *bdiag, int *lane_width) {
+  if (!ctx) return SLRF_EINVAL;
+  if (group) *group = ctx->grp;
+  if (bdiag) *bdiag = ctx->bdiag;
+  if (lane_width) *lane_width = ctx->vec;
+  return SLRF_OK;
+}
+
 int slrf_apply(slrf_ctx *ctx, const double *X, int k, double *AX, double *BX, int fp32) {
   if (!ctx) return SLRF_EINVAL;
   if (ctx->status != SLRF_OK) return SLRF_ESTATE;
@@ -1241,7 +1288,7 @@ int slrf_apply(slrf_ctx *ctx, const double *X, int k, double *AX, double *BX, in
   if (fp32 && ctx->mixed && ctx->grp > 1) {
     // FP32 records (Jacobi-scaled values when the preconditioner is on: scale both sides by D^1/2)
     spmm_grp_real32(n, ctx->grp, ctx->ngroups, ctx->gptr, ctx->grec, ctx->iflags + 15, grp_real_blocks(ctx), X, k,
-                    k, ctx->dsqrt, ctx->x32, AX, BX, k, ctx->dsqrt, ctx->st);
+                    k, ctx->dsqrt, ctx->x32, AX, BX, k, ctx->dsqrt, ctx->st, ctx->bdiag != 0);
   } else if (fp32) {
     spmm_ab32(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, k, k, AX, BX, k, ctx->st);
   } else {

@@ -33,7 +33,7 @@ SYMBOLS = ("slrf_opts_default", "slrf_setup", "slrf_get_poles", "slrf_filter_app
            "slrf_rayleigh_ritz", "slrf_solve", "slrf_solve_host", "slrf_eig_grad", "slrf_destroy",
            "slrf_strerror", "slrf_last_error", "slrf_filter_apply_static", "slrf_setup_batched",
            "slrf_solve_batched", "slrf_destroy_batched", "slrf_tsgram", "slrf_tsgemm", "slrf_wait_selftest",
-           "slrf_apply")
+           "slrf_apply", "slrf_format")
 
 
 class SlrfError(RuntimeError):
@@ -53,7 +53,8 @@ class Opts(ct.Structure):
                 ("tol_inner", ct.c_double), ("tol_eig", ct.c_double), ("precision", ct.c_int),
                 ("warm_start", ct.c_int), ("lock", ct.c_int), ("use_graph", ct.c_int), ("nev", ct.c_int),
                 ("seed", ct.c_uint64), ("poles", ct.c_void_p), ("weights", ct.c_void_p), ("autotune", ct.c_int),
-                ("dense", ct.c_int), ("it_adapt", ct.c_int), ("precond", ct.c_int), ("group", ct.c_int)]
+                ("dense", ct.c_int), ("it_adapt", ct.c_int), ("precond", ct.c_int), ("group", ct.c_int),
+                ("bdiag", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -81,6 +82,7 @@ def lib() -> ct.CDLL:
         L.slrf_get_poles.argtypes = [vp, ct.POINTER(i), vp, vp]
         L.slrf_filter_apply.argtypes = [vp, vp, i, vp, vp]
         L.slrf_apply.argtypes = [vp, vp, i, vp, vp, i]
+        L.slrf_format.argtypes = [vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)]
         L.slrf_filter_stats.argtypes = [vp, vp, vp, vp]
         L.slrf_filter_timing.argtypes = [vp, vp, i, vp, vp, vp, vp]
         L.slrf_rayleigh_ritz.argtypes = [vp, vp, i, vp, vp, i, i, vp, vp, vp]
@@ -192,6 +194,12 @@ class Context:
         th = None if theta is None else _dev(theta, torch.float64)
         _check(lib().slrf_filter_apply(self.h, _ptr(X), k, _ptr(th), _ptr(U)), "slrf_filter_apply")
         return U
+
+    def format(self):
+        """(group, bdiag, lane_width) of the COCG SpMM format chosen at setup (see slrf_format)."""
+        g, bd, lw = ct.c_int(), ct.c_int(), ct.c_int()
+        _check(lib().slrf_format(self.h, ct.byref(g), ct.byref(bd), ct.byref(lw)), "slrf_format")
+        return g.value, bd.value, lw.value
 
     def apply(self, X: torch.Tensor, fp32: bool = False, want_a: bool = True, want_b: bool = True):
         """(A X, B X) with the context's matrices (see slrf_apply); an output not wanted is None."""

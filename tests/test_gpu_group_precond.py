@@ -11,6 +11,8 @@ COCG update counts.  Against the FP64 oracle the grouped path keeps the CSR path
 1e-8 of max |U| on the Laplacian, 3e-8 on the lognormal-modulus elasticity pencil (whose
 COCG amplifies rounding more; the CSR path measured 1.18e-8 there at It_max 9).
 
+B-diagonal records (slrf_opts.bdiag): bitwise equal to the general records (exact zeros).
+
 Jacobi preconditioner (slrf_opts.precond, reading R18): compared with the oracle's
 preconditioned COCG on the same scaled systems (D = diag(A)); the tolerances are those of
 the unpreconditioned parity tests (U to 1e-8 of max |U|, update counts identical).
@@ -76,6 +78,40 @@ def test_grouped_spmm_matches_the_csr_path(slrf_mod, elast, precision, G, family
         Uo, fo = orc.filter_apply(p.A(), p.B(), V1, th, so, wo, it, 1e-10)
         assert rel(out[G][1], Uo) <= (3e-8 if family == "elast" else 1e-8)
         assert np.array_equal(out[G][2], fo.iters)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precond", [0, 1])
+def test_b_diagonal_records_match_the_general_records(slrf_mod, elast, precision, precond):
+    """3-row groups of the elasticity pencil (B = M (x) I_3, node-major dofs) take B-diagonal
+    records (one B value per record, the row c mod 3); slrf_opts.bdiag = 0 keeps the general
+    records.  A general record's other two B values are exact zeros, and fma(0, x, s) = s, so
+    the two formats must give bitwise equal filtered blocks, products and update counts.  The
+    scalar Laplacian's 3-row groups never qualify (its B couples every row of a group)."""
+    p, _, gamma, _ = elast
+    k = 21
+    V1 = si.start_block(p.n, k, 8)
+    th = np.linspace(0.2, 1.4, k) * gamma
+    out = {}
+    for bd in (1, 0):
+        opts = slrf_mod.slrf_opts_default(it_max=9, precision=precision, group=3, bdiag=bd, precond=precond)
+        ctx = slrf_mod.Context(p.rowptr, p.col, p.valA, p.valB, gamma, k, opts)
+        g, used, lw = ctx.format()
+        assert g == 3 and used == bd and lw == (4 if precision == 1 else 1)
+        U0 = ctx.filter_apply(torch.from_numpy(V1))
+        U1 = ctx.filter_apply(torch.from_numpy(V1), torch.from_numpy(th))
+        its, _, _ = ctx.filter_stats(k)
+        AX, BX = ctx.apply(torch.from_numpy(V1), fp32=True)
+        out[bd] = (U0, U1, its, AX, BX)
+        ctx.close()
+    for a, b in zip(out[1][:2] + out[1][3:], out[0][:2] + out[0][3:]):
+        assert torch.equal(a, b)
+    assert np.array_equal(out[1][2], out[0][2])
+    lap = si.q1_scalar((10, 7, 7), shift=1e-3)
+    ctx = slrf_mod.Context(lap.rowptr, lap.col, lap.valA, lap.valB, 60.0, k,
+                           slrf_mod.slrf_opts_default(precision=precision, group=3))
+    assert ctx.format()[:2] == (3, 0)
+    ctx.close()
 
 
 @pytest.mark.parametrize("warm", [False, True])
