@@ -45,7 +45,7 @@ DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
 # DRAM bytes (read + write) of one full-width launch of the timed path's SpMM kernel, from an
 # ncu capture (profiles/cocg_spmm_grp_f32_elast_64.md: block 32, 2 tiles, scaled to the 30
 # tiles of block 480; traffic is linear in the tiles).  Valid for the kernel as captured.
-DEFAULT_TRAFFIC = {("elast_64", 1): 77.6e9}
+DEFAULT_TRAFFIC = {}
 
 
 def measured_hbm_gbs():
@@ -266,15 +266,20 @@ def cpu_baseline_sample(name: str, it_max: int, precond: int, n_found: int, col_
             "seconds_sampled": t_f + t_rr + t_sp}
 
 
-def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic):
+def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic, bdiag: bool = False):
     """Roofline of the fused shifted SpMM + COCG phase-1 launch (the dominant kernel) at k
-    columns x m poles: algorithmic flops 8 per (entry, complex column) + 32 per (row, complex
-    column), algorithmic bytes 5 complex entries per (row, column) (r, p, q read; p, q
-    written) + one pass over the pattern and both value arrays.  The bound is whichever of
-    the ALU (FP64 / FP32 FMA pipe) and HBM times is larger."""
+    columns x m poles: algorithmic flops 8 per (entry of the shared pattern, complex column)
+    + 32 per (row, complex column), algorithmic bytes 5 complex entries per (row, column) (r,
+    p, q read; p, q written) + one pass over the pattern and both value arrays.  With
+    B-diagonal records the kernel multiplies only B's nonzero entries, so its executed flops
+    count 4 per pattern entry (A) + 4 per nonzero of B; the ALU side of the roofline uses the
+    executed flops.  The bound is whichever of the ALU (FP64 / FP32 FMA pipe) and HBM times is
+    larger."""
     W = m * k
     es = 16 if precision == 0 else 8
-    flops = 8.0 * p.nnz * W + 32.0 * p.n * W
+    flops_alg = 8.0 * p.nnz * W + 32.0 * p.n * W
+    nnz_b = int((p.valB != 0).sum())
+    flops = (4.0 * p.nnz + 4.0 * nnz_b) * W + 32.0 * p.n * W if bdiag else flops_alg
     nbytes = 5.0 * es * p.n * W + p.nnz * (4 + 2 * (8 if precision == 0 else 4))
     hbm, hbm_note = measured_hbm_gbs()
     alu_peak = FP64_PEAK_TFLOPS if precision == 0 else FP32_PEAK_TFLOPS
@@ -289,11 +294,16 @@ def spmm_roofline(p, m: int, k: int, precision: int, spmm_ms: float, traffic):
                 "note": (f"FP{64 if precision == 0 else 32} FMA pipe bound ({flops / nbytes:.1f} flop/B); peak = 152 SMs "
                          f"x {2 if precision == 0 else 128} FMA/clock x 2 x 2.07 GHz (derived); HBM "
                          f"{nbytes / s / 1e9:.0f} GB/s = {nbytes / s / 1e9 / hbm:.2f} {hbm_note} {hbm:.0f} GB/s"),
-                "hbm_gbs_algorithmic": nbytes / s / 1e9, "flops_per_launch": flops, "bytes_per_launch": nbytes}
+                "hbm_gbs_algorithmic": nbytes / s / 1e9, "flops_per_launch": flops, "flops_pattern_per_launch": flops_alg,
+                "bytes_per_launch": nbytes, "b_diagonal_records": bdiag}
     achieved = nbytes / s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": kern, "note": f"{hbm_note} hbm_gbs; {flops / s / 1e12:.1f} TFLOP/s",
-            "flops_per_launch": flops, "bytes_per_launch": nbytes}
+            "traffic": traffic, "kernel": kern,
+            "note": (f"{hbm_note} hbm_gbs; {flops / s / 1e12:.1f} TFLOP/s executed "
+                     f"({flops / s / 1e12 / alu_peak:.2f} of the FP{64 if precision == 0 else 32} peak)"
+                     + ("; B-diagonal records: only B's nonzeros multiplied" if bdiag else "")),
+            "flops_per_launch": flops, "flops_pattern_per_launch": flops_alg, "bytes_per_launch": nbytes,
+            "b_diagonal_records": bdiag}
 
 
 def paper_table_records(slrf, si, torch):
@@ -468,12 +478,14 @@ def main():
     # kernel-level roofline of the dominant kernel (the fused shifted SpMM + COCG phase 1)
     with torch.cuda.stream(stream):
         tim = ctx.filter_timing(V0[:, :wl.block])
+    fmt = ctx.format()
     ctx.close()
     spmm_ms = tim["ms_spmm"] / max(tim["n_spmm"], 1)
     traffic = args.traffic_bytes
     if traffic is None and args.group == 0:
         traffic = DEFAULT_TRAFFIC.get((args.workload, prec))
-    roof = spmm_roofline(p, wl.m, wl.block, prec, spmm_ms, traffic)
+    roof = spmm_roofline(p, wl.m, wl.block, prec, spmm_ms, traffic, bdiag=fmt[1] == 1)
+    roof["spmm_format"] = {"group": fmt[0], "b_diagonal": fmt[1], "lane_width": fmt[2]}
     roof["update_ms"] = tim["ms_update"] / max(tim["n_update"], 1)
     roof["spmm_ms"] = spmm_ms
     # ---- the other precision on the same workload (FP64 vs mixed at equal residual)
