@@ -819,7 +819,9 @@ def reference_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": (time.perf_counter() - t_start) * 1e3 / (args.warmup + args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {desc}", "it_max": cnt["it_max"],
-                       "precision": cnt.get("precision", 0), "precond": cnt.get("precond", 0),
+                       "precision": 0, "precond": cnt.get("precond", 0),
+                       "counts_from": ("the GPU solve at these settings, precision %d (outer iterations, "
+                                       "column-iterations, mean active block)" % cnt.get("precision", 0)),
                        "l2": "n/a (host)", "parallelism": "replicas x1"},
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "eigenpairs/s", "cores": vals[-1]["cores"], "kind": "oracle",
