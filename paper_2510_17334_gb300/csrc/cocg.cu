@@ -1570,6 +1570,73 @@ void spmm_grp_real32(int64_t n, int G, int64_t ngroups, const int64_t *gptr, con
   }
 }
 
+// FP64 real products through FP64 B-diagonal records (3-row groups): a lane takes one
+// double2 -- two adjacent real columns -- of the padded FP64 copy x64, so a warp covers 64
+// columns per tile and the FMAs are those of the complex FP64 SpMM (A and B products per
+// gathered row: 3 + 1).  Output row i is multiplied by yscale[i] (null: 1).
+struct GrpReal64 {
+  int64_t n, ngroups;
+  const int64_t *gptr;
+  const unsigned char *grec;
+  int *err;
+  int nrb;
+  const double *x;
+  int ldx;
+  int k;
+  double *YA, *YB;
+  int ldy;
+  const double *yscale;
+};
+int grp_real64_ld(int k) { return (k + 63) / 64 * 64; }
+__global__ void to_f64_scaled_kernel(int64_t n, int k, const double *__restrict__ X, int ldx,
+                                     const double *__restrict__ s, double *__restrict__ Y, int ldy) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ldy) return;
+  const int64_t i = t / ldy;
+  const int c = (int)(t - i * ldy);
+  Y[t] = c < k ? (s != nullptr ? X[i * ldx + c] * s[i] : X[i * ldx + c]) : 0.0;
+}
+__global__ void __launch_bounds__(kThreads, (cocg_grp_minb<double, 1, 3>())) spmm_grp_real64_kernel(const GrpReal64 a) {
+  constexpr int RS = grec_bytes<double, 3, true>();
+  extern __shared__ __align__(128) unsigned char grp_smem[];
+  __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = (int)blockIdx.y * 64 + 2 * lane;  // this lane's two real columns
+  const int64_t gstride = (int64_t)a.nrb * kWarps;
+  const int64_t gfirst = (int64_t)blockIdx.x * kWarps + warp;
+  if (gfirst >= a.ngroups) return;  // warp-uniform; the kernel has no block-wide barrier
+  auto epi = [&](int64_t g, const double2 (&sa)[3][1], const double2 (&sb)[3][1]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int64_t i = g * 3 + j;
+      if (i >= a.n) continue;
+      const double ys = a.yscale != nullptr ? a.yscale[i] : 1.0;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = c0 + e;
+        if (c < a.k) {
+          if (a.YA) a.YA[(size_t)i * a.ldy + c] = ys * (e ? sa[j][0].y : sa[j][0].x);
+          if (a.YB) a.YB[(size_t)i * a.ldy + c] = ys * (e ? sb[j][0].y : sb[j][0].x);
+        }
+      }
+    }
+  };
+  grp_walk<double, 1, 3, true>(a.ngroups, a.gptr, a.grec, a.err, a.n, gfirst, gstride,
+                               reinterpret_cast<const char *>(a.x + c0), (unsigned)a.ldx * 8u,
+                               grp_smem + (size_t)warp * 2 * grp_chunk<double, true>() * RS, s_bar[warp], epi);
+}
+void spmm_grp_real64(int64_t n, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err, int nrb,
+                     const double *X, int ldx, int k, const double *xscale, double *x64, double *YA, double *YB,
+                     int ldy, const double *yscale, cudaStream_t st) {
+  if (n <= 0 || k <= 0 || nrb <= 0) return;
+  const int ld64 = grp_real64_ld(k);
+  const int64_t tot = n * ld64;
+  to_f64_scaled_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, k, X, ldx, xscale, x64, ld64);
+  GrpReal64 a{n, ngroups, gptr, grec, err, nrb, x64, ld64, k, YA, YB, ldy, yscale};
+  const dim3 grid((unsigned)nrb, (unsigned)(ld64 / 64));
+  spmm_grp_real64_kernel<<<grid, kThreads, grp_smem_bytes<double, 3, true>(), st>>>(a);
+}
+
 template <typename R, int V, int G> static void grp_attrs_v() {
   const int sm = grp_smem_bytes<R, G>();
   cudaFuncSetAttribute(cocg_spmm_grp_kernel<R, V, G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -1596,6 +1663,8 @@ template <typename R, int G> static void grp_attrs() {
 void cocg_kernel_attrs() {
   static bool done = false;
   if (done) return;
+  cudaFuncSetAttribute(spmm_grp_real64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       grp_smem_bytes<double, 3, true>());
   grp_attrs<float, 2>();
   grp_attrs<float, 3>();
   grp_attrs<float, 4>();

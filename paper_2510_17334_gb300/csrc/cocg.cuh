@@ -213,6 +213,13 @@ void grp_bd_detect(int64_t n, int64_t ngroups, const int64_t *gptr, const unsign
 // General records -> B-diagonal records (nrec of them).
 template <typename R>
 void grp_bd_convert(int64_t nrec, const unsigned char *rec, unsigned char *bdrec, cudaStream_t st);
+// FP64 real products through FP64 B-diagonal records of 3-row groups: YA = A X and/or YB = B X
+// (either may be null), X first copied to x64 ([n][grp_real64_ld(k)], padding zero) with row i
+// multiplied by xscale[i] (null: 1), output row i by yscale[i] (null: 1).
+int grp_real64_ld(int k);
+void spmm_grp_real64(int64_t n, int64_t ngroups, const int64_t *gptr, const unsigned char *grec, int *err, int nrb,
+                     const double *X, int ldx, int k, const double *xscale, double *x64, double *YA, double *YB,
+                     int ldy, const double *yscale, cudaStream_t st);
 // Resident blocks per SM of the grouped SpMM of height G (after cocg_kernel_attrs; 0 on error).
 int grp_blocks_per_sm(int G, bool fp32, bool bd = false);
 

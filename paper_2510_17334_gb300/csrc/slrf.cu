@@ -90,6 +90,8 @@ struct slrf_ctx {
   int64_t rpb_tuned = 0;             // autotuned COCG rows per block (0 = default)
   int grp_bpsm = 0;                  // resident blocks per SM of the grouped SpMM in use
   int bdiag = 0;                     // the grouped records are B-diagonal (see grec_col)
+  unsigned char *grec64 = nullptr;   // mixed path: FP64 B-diagonal records of the same groups
+  double *x64 = nullptr;             // padded FP64 copy of a real block for the grouped FP64 products
   // real n x L blocks (ld = L)
   double *V = nullptr, *AV = nullptr, *BV = nullptr, *G = nullptr, *AG = nullptr, *BG = nullptr;
   double *U = nullptr, *U2 = nullptr, *BU = nullptr, *Vt = nullptr, *AVt = nullptr, *BVt = nullptr;
@@ -253,6 +255,8 @@ static int grec_size(int G, bool fp32) { return grec_bytes_rt(G, fp32); }
 static void drop_groups(slrf_ctx *ctx) {
   dfree(ctx, ctx->gptr);
   dfree(ctx, ctx->grec);
+  dfree(ctx, ctx->grec64);
+  ctx->grec64 = nullptr;
   ctx->gptr = nullptr;
   ctx->grec = nullptr;
   ctx->grp = 1;
@@ -326,6 +330,22 @@ static int build_groups(slrf_ctx *ctx, int G) {
       dfree(ctx, ctx->grec);
       ctx->grec = bdrec;
       bd = 1;
+      if (ctx->mixed) {
+        // FP64 B-diagonal records of the same groups for the FP64 real products of the outer step
+        unsigned char *gen64 = nullptr, *bd64 = nullptr;
+        if ((rc = dalloc(ctx, &gen64, (size_t)off[ng] * grec_bytes_rt(3, false) + 16)) != SLRF_OK) return rc;
+        if ((rc = dalloc(ctx, &bd64, (size_t)off[ng] * grec_bytes_rt(3, false, true) + 16)) != SLRF_OK) return rc;
+        grp_fill<double>(ctx->n, 3, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->gptr, gen64, ctx->st);
+        grp_bd_convert<double>(off[ng], gen64, bd64, ctx->st);
+        if (cudaMemsetAsync(dflag, 0, sizeof(int), ctx->st) != cudaSuccess) return SLRF_ECUDA;
+        grp_check<double>(ctx->n, 3, ng, ctx->gptr, bd64, dflag, ctx->sm_count * 4, ctx->st, true);
+        if (cudaMemcpyAsync(&bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+          return SLRF_ECUDA;
+        dfree(ctx, gen64);
+        if (bad) dfree(ctx, bd64);
+        else ctx->grec64 = bd64;
+      }
     }
   }
   ctx->bdiag = bd;
@@ -389,10 +409,31 @@ static int64_t row_blocks(const slrf_ctx *ctx) {
   const int per_sm = (ctx->grp > 1 && ctx->grp_bpsm > 0) ? std::min(ctx->grp_bpsm, 4) : 4;
   return (int64_t)ctx->sm_count * per_sm;
 }
+// FP64 B-diagonal records of the context, or null: an FP64 context's own records, or the extra
+// FP64 records of a mixed context
+static const unsigned char *rec64(const slrf_ctx *ctx) {
+  if (ctx->grp != 3 || !ctx->bdiag) return nullptr;
+  return ctx->mixed ? ctx->grec64 : ctx->grec;
+}
+// FP64 products A X, B X (either output may be null) with the stored matrices: through the FP64
+// B-diagonal records when the context has them (scaled back by D^1/2 when they hold the
+// Jacobi-scaled values), else the CSR kernel.
+static void real_products64(slrf_ctx *ctx, const double *X, int ldx, int k, double *YA, double *YB, int ldy,
+                            cudaStream_t st);
+
 // row blocks of the grouped real SpMM: one resident wave, no more than there are stripes
 static int grp_real_blocks(const slrf_ctx *ctx) {
   const int64_t stripes = (ctx->ngroups + kWarps - 1) / kWarps;
   return (int)std::max<int64_t>(1, std::min<int64_t>(row_blocks(ctx), stripes));
+}
+static void real_products64(slrf_ctx *ctx, const double *X, int ldx, int k, double *YA, double *YB, int ldy,
+                            cudaStream_t st) {
+  const unsigned char *r64 = rec64(ctx);
+  if (r64 != nullptr && ctx->x64 != nullptr)
+    spmm_grp_real64(ctx->n, ctx->ngroups, ctx->gptr, r64, ctx->iflags + 15, grp_real_blocks(ctx), X, ldx, k,
+                    ctx->dsqrt, ctx->x64, YA, YB, ldy, ctx->dsqrt, st);
+  else
+    spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, YA, YB, ldy, st);
 }
 
 // COCG arguments of one filter apply of this context (k columns, optional warm start).
@@ -571,13 +612,13 @@ static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
   const cudaStream_t st = ctx->st;
   const int L = ctx->L;
   if (theta == nullptr) {
-    spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, nullptr, ctx->G, L, st);
+    real_products64(ctx, X, ldx, k, nullptr, ctx->G, L, st);
     ctx->launches += 1;
   } else {
     const double *AX = AXp, *BX = BXp;
     int ldab = L;
     if (AX == nullptr || BX == nullptr) {
-      spmm_real(ctx->n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, ldx, k, ctx->AG, ctx->BG, L, st);
+      real_products64(ctx, X, ldx, k, ctx->AG, ctx->BG, L, st);
       AX = ctx->AG;
       BX = ctx->BG;
       ctx->launches += 1;
@@ -596,6 +637,9 @@ static int filter_prep(slrf_ctx *ctx, const double *X, int ldx, int k, const dou
                     ctx->G, L, k, nullptr, ctx->x32, ctx->AG, ctx->BG, L, nullptr, st, ctx->bdiag != 0);
   else if (ctx->mixed)
     spmm_ab32(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
+  else if (rec64(ctx) != nullptr && ctx->x64 != nullptr)  // records hold the values the solves use
+    spmm_grp_real64(ctx->n, ctx->ngroups, ctx->gptr, rec64(ctx), ctx->iflags + 15, grp_real_blocks(ctx), ctx->G, L, k,
+                    nullptr, ctx->x64, ctx->AG, ctx->BG, L, nullptr, st);
   else
     spmm_real(ctx->n, ctx->rowptr, ctx->col, cocg_valA(ctx), cocg_valB(ctx), ctx->G, L, k, ctx->AG, ctx->BG, L, st);
   ctx->launches += 1;
@@ -772,7 +816,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st, ctx->iflags + 11);
   tsgemm(ctx, n, U, L, k, ctx->Rinv, k, k, U1, L, 1.0, 0.0, true);
   // pass 2 and projection
-  spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, U1, L, k, AU1, ctx->BU, L, st);
+  real_products64(ctx, U1, L, k, AU1, ctx->BU, L, st);
   tsgram(ctx, n, U1, L, k, ctx->BU, L, k, ctx->Gm, k, true);
   tsgram(ctx, n, U1, L, k, AU1, L, k, ctx->Hm, k, true);
   chol_inv(k, ctx->Gm, k, ctx->Rinv, k, ctx->iflags + 4, st);
@@ -791,7 +835,7 @@ static int rr_impl(slrf_ctx *ctx, double *U, int k, const double *X, const doubl
     tsgemm(ctx, n, AU1, L, k, ctx->Wm, k, k, ctx->AVt, L, 1.0, 0.0, false);
     tsgemm(ctx, n, ctx->BU, L, k, ctx->Wm, k, k, ctx->BVt, L, 1.0, 0.0, false);
   } else {
-    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
+    real_products64(ctx, ctx->Vt, L, k, ctx->AVt, ctx->BVt, L, st);
     ctx->launches += 1;
   }
   ritz_residuals(n, k, ctx->Vt, ctx->AVt, ctx->BVt, L, ctx->theta, ctx->res, ctx->res_paper, ctx->sgn, ctx->work, st);
@@ -1102,7 +1146,8 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   const size_t blocks = 16 * sizeof(double) * (size_t)n * L;
   const size_t matrix = (size_t)ctx->nnz * (4 + 16 + (ctx->mixed ? 8 : 0)) + 8 * (size_t)(n + 1);
   const size_t refine = (ctx->mixed && o.refine_max > 1) ? 16 * (size_t)n * ctx->Wmax : 0;
-  const size_t uacc = 8 * (size_t)n * (ctx->Wmax / ctx->mp) + (ctx->mixed ? 4 * (size_t)n * grp_real32_ld(L) : 0);
+  const size_t uacc = 8 * (size_t)n * (ctx->Wmax / ctx->mp) + (ctx->mixed ? 4 * (size_t)n * grp_real32_ld(L) : 0) +
+                      8 * (size_t)n * grp_real64_ld(L);
   const size_t need = (state + blocks + matrix + refine + uacc) + 8 * partial + (64u << 20);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(SLRF_ECUDA);
@@ -1211,6 +1256,7 @@ int slrf_setup(slrf_ctx **out, const slrf_csr_pair *pc, double gamma, int block_
   }
   AL(ctx->uacc, (size_t)n * (ctx->Wmax / ctx->mp));
   if (ctx->mixed) AL(ctx->x32, (size_t)n * grp_real32_ld(L));
+  AL(ctx->x64, (size_t)n * grp_real64_ld(L));
   if (ctx->dsc != nullptr) {
     AL(ctx->dsqrt, (size_t)n);
     recip_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->st>>>(n, ctx->dsc, ctx->dsqrt);
@@ -1292,7 +1338,7 @@ int slrf_apply(slrf_ctx *ctx, const double *X, int k, double *AX, double *BX, in
   } else if (fp32) {
     spmm_ab32(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, k, k, AX, BX, k, ctx->st);
   } else {
-    spmm_real(n, ctx->rowptr, ctx->col, ctx->valA, ctx->valB, X, k, k, AX, BX, k, ctx->st);
+    real_products64(ctx, X, k, k, AX, BX, k, ctx->st);
   }
   CKL();
   return SLRF_OK;

@@ -86,8 +86,12 @@ def test_b_diagonal_records_match_the_general_records(slrf_mod, elast, precision
     """3-row groups of the elasticity pencil (B = M (x) I_3, node-major dofs) take B-diagonal
     records (one B value per record, the row c mod 3); slrf_opts.bdiag = 0 keeps the general
     records.  A general record's other two B values are exact zeros, and fma(0, x, s) = s, so
-    the two formats must give bitwise equal filtered blocks, products and update counts.  The
-    scalar Laplacian's 3-row groups never qualify (its B couples every row of a group)."""
+    the COCG SpMM and the FP32 products agree bitwise (the FP32 A X, B X below).  The FP64
+    real products of the filter start run through FP64 B-diagonal records in one case and
+    the CSR kernel in the other (another summation order), so the filtered blocks agree to
+    rounding amplified over the It_max steps: 1e-12 of max |U| in FP64, 1e-6 in FP32, with
+    identical update counts.  The scalar Laplacian's 3-row groups never qualify (its B
+    couples every row of a group)."""
     p, _, gamma, _ = elast
     k = 21
     V1 = si.start_block(p.n, k, 8)
@@ -104,7 +108,10 @@ def test_b_diagonal_records_match_the_general_records(slrf_mod, elast, precision
         AX, BX = ctx.apply(torch.from_numpy(V1), fp32=True)
         out[bd] = (U0, U1, its, AX, BX)
         ctx.close()
-    for a, b in zip(out[1][:2] + out[1][3:], out[0][:2] + out[0][3:]):
+    tol = 1e-12 if precision == 0 else 1e-6
+    for a, b in zip(out[1][:2], out[0][:2]):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= tol
+    for a, b in zip(out[1][3:], out[0][3:]):
         assert torch.equal(a, b)
     assert np.array_equal(out[1][2], out[0][2])
     lap = si.q1_scalar((10, 7, 7), shift=1e-3)
