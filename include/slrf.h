@@ -160,8 +160,10 @@ int slrf_filter_apply(slrf_ctx *ctx, const double *X, int k, const double *theta
  * both) for a real block X (device, n x k row-major, k <= L); AX and BX (device, n x k
  * row-major) may alias neither X nor each other.  These are the products the outer
  * iteration of Alg. 2 forms (the real sweep that starts the filter, the Gram matrices of
- * the B-orthonormalisation and Rayleigh-Ritz, Sec. 4).  fp32 = 0: FP64 products and sums
- * (the stored CSR values).  fp32 = 1: FP32 products and sums, through the grouped-row
+ * the B-orthonormalisation and Rayleigh-Ritz, Sec. 4).  fp32 = 0: FP64 products and sums,
+ * through FP64 B-diagonal grouped records when the context has them (see slrf_opts.bdiag;
+ * only B's nonzeros multiplied, scaled back by D^1/2 with precond = 1), else through the
+ * stored CSR values.  fp32 = 1: FP32 products and sums, through the grouped-row
  * records of a precision = 1 context when it has them (G > 1; with precond = 1 those
  * hold D^-1/2 A D^-1/2 and D^-1/2 B D^-1/2, and the result is scaled back by D^1/2 on both
  * sides), else through the CSR values rounded to FP32.  Asynchronous on the context
