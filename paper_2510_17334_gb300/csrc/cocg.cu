@@ -1712,7 +1712,10 @@ template void cocg_spmm<float>(const CocgArgs<float> &, cudaStream_t, bool);
 template void cocg_residual<float>(const CocgArgs<float> &, cudaStream_t);
 
 // ------------------------------------------------------------------------------ batched launchers
-static int batch_grid(int total) { return total < 152 * 4 ? total : 152 * 4; }
+static int batch_grid(int total) {
+  const int cap = device_sm_count() * 4;
+  return total < cap ? total : cap;
+}
 
 template <typename R> void cocg_init_batched_launch(const CocgArgs<R> *args, const int *prefix, int P, int total,
                                                     cudaStream_t st) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -187,6 +188,24 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                    su32(dst)),
                "l"(src), "r"(bytes), "r"(su32(bar))
                : "memory");
+}
+
+// ---------------------------------------------------------------- host: grid sizing
+// Multiprocessors of the current device, queried once per device and cached (grids of the
+// grid-stride kernels and the split counts of the tall-skinny products are sized from it).
+inline int device_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  int v = dev < kMaxDev ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();  // clear the failed query
+    v = 1;
+  }
+  if (dev < kMaxDev) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 }  // namespace slrf

@@ -362,7 +362,7 @@ __global__ void check_finite_kernel(int64_t count, const double *x, int *flag) {
 void check_finite(int64_t count, const double *x, int *flag, cudaStream_t st) {
   if (count <= 0) return;
   int blocks = (int)((count + 255) / 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
   check_finite_kernel<<<blocks, 256, 0, st>>>(count, x, flag);
 }
 
@@ -478,7 +478,7 @@ __global__ void gram_reduce_kernel(int k1, int k2, int nz, bool sym, const doubl
 
 static int gram_chunks(int64_t n, int k1, int k2) {
   const int tiles = ((k1 + kGT - 1) / kGT) * ((k2 + kGT - 1) / kGT);
-  int nz = (2 * 152 + tiles - 1) / tiles;
+  int nz = (2 * device_sm_count() + tiles - 1) / tiles;
   const int64_t maxz = (n + 255) / 256;
   if (nz > maxz) nz = (int)maxz;
   if (nz < 1) nz = 1;

@@ -463,16 +463,7 @@ __global__ void oz_gram_finalize_kernel(int k1, int k2, int nsplit, int MR, int 
                                                                      : scalbn(s, ea + eb - 16);
 }
 
-int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+int num_sms() { return device_sm_count(); }
 
 void set_smem_attrs() {
   static bool done = false;
@@ -498,7 +489,7 @@ GramPlan gram_plan(int64_t n, int k1, int k2, bool sym) {
   }
   g.KB = (int)(pad32(n) / 32);
   const int chunks = std::max(1, (g.KB + kChunkKB - 1) / kChunkKB);
-  int ns = std::max(1, 152 / g.tiles);
+  int ns = std::max(1, num_sms() / g.tiles);
   ns = std::max(ns, (chunks + kMaxChunksPerCta - 1) / kMaxChunksPerCta);
   ns = std::min(ns, chunks);
   g.kb_per_split = ((chunks + ns - 1) / ns) * kChunkKB;
@@ -539,11 +530,11 @@ GemmLayout gemm_layout(int64_t n, int k1, int k2) {
 }  // namespace
 
 size_t oz_work_bytes(int64_t n, int k1, int k2) {
-  // any k1' <= k1, k2' <= k2, symmetric or not: at most max(152, chunks / 64) splits of
+  // any k1' <= k1, k2' <= k2, symmetric or not: at most max(SMs, chunks / 64) splits of
   // partial tiles no larger than the k1 x k2 tile grid
   const int kmax = std::max(k1, k2);
   const int64_t chunks = std::max<int64_t>(1, (pad32(n) / 32 + kChunkKB - 1) / kChunkKB);
-  const size_t splits = (size_t)std::max<int64_t>(152, (chunks + kMaxChunksPerCta - 1) / kMaxChunksPerCta);
+  const size_t splits = (size_t)std::max<int64_t>(num_sms(), (chunks + kMaxChunksPerCta - 1) / kMaxChunksPerCta);
   const size_t part = splits * (size_t)((kmax + kTM - 1) / kTM * kTM) * (size_t)pad32(kmax) * sizeof(double);
   const size_t gram = up256((size_t)2 * pad32(kmax) * sizeof(int)) + 2 * up256(digit_bytes(kmax, n)) + part;
   return std::max(gram, gemm_layout(n, kmax, kmax).bytes) + 256;

@@ -64,7 +64,7 @@ struct slrf_ctx {
   int64_t ngroups = 0;
   int64_t *gptr = nullptr;
   unsigned char *grec = nullptr;
-  int sm_count = 152;  // multiprocessors of the device (grid sizing)
+  int sm_count = 0;  // multiprocessors of the device (grid sizing), queried at setup
   // pole table
   double2 *sig = nullptr, *wt = nullptr;
   float2 *sig32 = nullptr;
