@@ -46,7 +46,7 @@ DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
 # grouped kernel with B-diagonal records), from an ncu capture (profiles/
 # cocg_spmm_grp_f32_elast_64.md: block 32, 2 tiles, scaled to the 30 tiles of block 480;
 # traffic is linear in the tiles).  Valid for the kernel as captured.
-DEFAULT_TRAFFIC = {("elast_64", 1): 74.1e9}
+DEFAULT_TRAFFIC = {("elast_64", 1): 74.2e9}
 
 
 def measured_hbm_gbs():

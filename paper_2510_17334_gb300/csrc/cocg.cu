@@ -44,7 +44,7 @@
 #define SLRF_GRP_MINB 2
 #endif
 #ifndef SLRF_GRP_UNROLL_BD
-#define SLRF_GRP_UNROLL_BD 2
+#define SLRF_GRP_UNROLL_BD 4
 #endif
 // Per-record check of the gathered column in the grouped SpMM (1), or none (0): the records
 // are built on the device from a pattern validated at setup and checked once after the
