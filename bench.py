@@ -42,11 +42,13 @@ DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 23
 DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 23, "bar1d_2000": 200}
 # Jacobi preconditioner on by default for the elasticity boxes (reading R18)
 DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
-# DRAM bytes (read + write) of one full-width launch of the timed path's SpMM kernel (the
-# grouped kernel with B-diagonal records), from an ncu capture (profiles/
-# cocg_spmm_grp_f32_elast_64.md: block 32, 2 tiles, scaled to the 30 tiles of block 480;
-# traffic is linear in the tiles).  Valid for the kernel as captured.
-DEFAULT_TRAFFIC = {("elast_64", 1): 74.2e9}
+# DRAM bytes (read + write) of one full-width launch of the timed path's SpMM kernel, from
+# an ncu capture of the kernel as it is now (block 32, 2 tiles, scaled to the 30 tiles of
+# block 480; traffic is linear in the tiles), keyed by (workload, precision); an entry is
+# dropped when the kernel changes.  The grouped kernel with B-diagonal records read 74.2 GB
+# per launch when it staged 63-record chunks; the 81-record chunks it stages now have not
+# been captured, so the roofline's traffic is null.
+DEFAULT_TRAFFIC = {}
 
 
 def measured_hbm_gbs():

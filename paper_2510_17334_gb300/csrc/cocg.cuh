@@ -119,9 +119,12 @@ inline int grec_bytes_rt(int G, bool fp32, bool bd = false) {
 #ifndef SLRF_GRP_CHUNK64
 #define SLRF_GRP_CHUNK64 64
 #endif
-// (B-diagonal records: 63, whole node triples)
+// B-diagonal records: whole node triples per chunk (a multiple of 3).
+#ifndef SLRF_GRP_CHUNK_BD
+#define SLRF_GRP_CHUNK_BD 81
+#endif
 template <typename R, bool BD = false> __host__ __device__ constexpr int grp_chunk() {
-  return BD ? 63 : (sizeof(R) == 4 ? SLRF_GRP_CHUNK32 : SLRF_GRP_CHUNK64);
+  return BD ? SLRF_GRP_CHUNK_BD : (sizeof(R) == 4 ? SLRF_GRP_CHUNK32 : SLRF_GRP_CHUNK64);
 }
 // Dynamic shared memory of the grouped SpMM: two chunk buffers per warp.
 template <typename R, int G, bool BD = false> __host__ __device__ constexpr int grp_smem_bytes() {
