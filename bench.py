@@ -52,7 +52,7 @@ DEFAULT_TRAFFIC = {}
 
 
 def measured_hbm_gbs():
-    """Copy bandwidth of the GB300s (MEASURED_PEAKS.json, driver-written), else the
+    """Measured GB300 copy bandwidth (MEASURED_PEAKS.json at the repository root), else the
     fallback figure of an earlier measurement."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -386,7 +386,7 @@ def main():
     ap.add_argument("--compare-it-max", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=2, help="whole solves from host buffers for the e2e figure")
     ap.add_argument("--traffic-bytes", type=float, default=None,
-                    help="DRAM bytes of one SpMM launch from an ncu capture of this build (else null)")
+                    help="DRAM bytes of one SpMM launch from an ncu capture of the current kernel (else null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--filter-only", type=int, default=0, metavar="L",
                     help="profiling aid: kernel-by-kernel timing of filter applies with block L, no JSON line")
