@@ -40,7 +40,7 @@ DEFAULT_WORKLOAD = "elast_64"
 # 23.5 / 18.2 eigenpairs/s (15 / 14 / 13 / 13 / 12 / 12 / 13 outer steps)
 DEFAULT_IT_MAX = {"q1_lap_41": 8, "elast_32": 20, "elast_48": 20, "elast_64": 23, "bar1d_2000": 200}
 DEFAULT_IT_MAX_FP64 = {"q1_lap_41": 8, "elast_32": 40, "elast_48": 40, "elast_64": 23, "bar1d_2000": 200}
-# Jacobi preconditioner on by default for the elasticity boxes (reading R18)
+# Jacobi preconditioner (D = diag(A), applied on both sides) on by default for the elasticity boxes
 DEFAULT_PRECOND = {"elast_32": 1, "elast_48": 1, "elast_64": 1}
 # DRAM bytes (read + write) of one full-width launch of the timed path's SpMM kernel, from
 # an ncu capture of the kernel as it is now (block 32, 2 tiles, scaled to the 30 tiles of

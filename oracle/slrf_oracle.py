@@ -50,7 +50,8 @@ E_NOCONV = -7
 
 
 # ----------------------------------------------------------------------------------------
-# a1: poles and weights (Sec. 2.2; reading R1)
+# Poles and weights (Sec. 2.2 takes the formula from a companion paper: midpoint abscissae,
+# weights fitted to the indicator of (0, gamma] with a Tikhonov term)
 # ----------------------------------------------------------------------------------------
 def slrf_poles(m: int, gamma: float, alpha: float = 1.0, beta: float = 0.01, band: float = 1.3,
                n_in: int = 3000, n_out: int = 3000, t_max: float = 51.0):
@@ -114,7 +115,7 @@ def filter_value(t, sigma, w):
 
 
 # ----------------------------------------------------------------------------------------
-# a3/a4: COCG on (A - sigma B) y = b, columns independent
+# COCG on (A - sigma B) y = b, columns independent
 # ----------------------------------------------------------------------------------------
 @dataclass
 class CocgInfo:
@@ -139,7 +140,8 @@ def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarra
     y0 = 0 it is the usual ||r||/||b||.
     A column whose mu or rho vanishes (or is not finite) stops and is flagged.
 
-    Jacobi preconditioning (reading R18; the paper preconditions its inner solver, Sec. 3.2):
+    Jacobi preconditioning (the paper preconditions its inner solver, Sec. 3.2; here the
+    diagonal of A, applied on both sides so that the system stays complex symmetric):
     with ``d`` (the positive diagonal of D) the same iteration runs on the symmetrically
     scaled system  (D^-1/2 M D^-1/2) z = D^-1/2 b  from z0 = D^1/2 y0, and y = D^-1/2 z.
     The scaled matrix is still complex symmetric, so COCG applies unchanged; residuals,
@@ -189,7 +191,7 @@ def cocg(A: sp.csr_matrix, B: sp.csr_matrix, sigma, b: np.ndarray, y0: np.ndarra
 
 
 # ----------------------------------------------------------------------------------------
-# a2-a5: filter apply  U = sum_j 2 Re(w_j Y_j),  (A - sigma_j B) Y_j = B V
+# Filter apply  U = sum_j 2 Re(w_j Y_j),  (A - sigma_j B) Y_j = B V
 # ----------------------------------------------------------------------------------------
 @dataclass
 class FilterInfo:
@@ -225,7 +227,7 @@ def filter_apply(A, B, V, theta, sigma, w, it_max, tol, d=None):
 
 
 # ----------------------------------------------------------------------------------------
-# a6: B-orthogonalise against the locked vectors (first step of the outer update of Alg. 2), CGS2
+# B-orthogonalise against the locked vectors (first step of the outer update of Alg. 2), CGS2
 # ----------------------------------------------------------------------------------------
 def b_orth(U, X, BX):
     """U <- U - X (X^T B U), twice, using the stored B X."""
@@ -235,7 +237,7 @@ def b_orth(U, X, BX):
 
 
 # ----------------------------------------------------------------------------------------
-# a7: Cholesky-QR2 in the B-inner product
+# Cholesky-QR2 in the B-inner product
 # ----------------------------------------------------------------------------------------
 def cholqr2(U, B):
     """Two passes of G = U^T B U, G = R^T R, U <- U R^{-1}.  Returns (U, status)."""
@@ -251,7 +253,7 @@ def cholqr2(U, B):
 
 
 # ----------------------------------------------------------------------------------------
-# a8: Rayleigh-Ritz on the B-orthonormal basis (Alg. 2)
+# Rayleigh-Ritz on the B-orthonormal basis (Alg. 2)
 # ----------------------------------------------------------------------------------------
 def rayleigh_ritz(U, A):
     """theta ascending and V = U S from the eigenpairs of H = U^T A U."""
@@ -270,7 +272,7 @@ def sign_normalise(V):
 
 
 # ----------------------------------------------------------------------------------------
-# a9: residuals, convergence, locking
+# Residuals, convergence, locking
 # ----------------------------------------------------------------------------------------
 def ritz_residuals(A, B, V, theta):
     """Relative residual ||A v - theta B v||_2 / ||A v||_2 per column, and the paper's
@@ -363,7 +365,7 @@ def enhanced_slrf(A, B, gamma, V1, m=8, it_max=40, tol_in=1e-10, tol_eig=1e-8, o
 
 
 # ----------------------------------------------------------------------------------------
-# a12: eigenvalue adjoint on the pattern
+# Eigenvalue adjoint on the pattern
 # ----------------------------------------------------------------------------------------
 def eig_grad_values(rowptr, col, evals, X, g_eval):
     """dL/dA_e and dL/dB_e for L with dL/dlambda_i = g_i, every stored entry e = (r, c) an
@@ -379,7 +381,7 @@ def eig_grad_values(rowptr, col, evals, X, g_eval):
 
 
 # ----------------------------------------------------------------------------------------
-# a13: eigenvector adjoint on the pattern (dense reference for small pencils)
+# Eigenvector adjoint on the pattern (dense reference for small pencils)
 # ----------------------------------------------------------------------------------------
 def eig_grad_full(rowptr, col, A, B, evals, X, g_eval, g_X):
     """dL/dA_e, dL/dB_e for a loss with dL/dlambda_i = g_i and dL/dx_i = g_x_i (x_i

@@ -1,4 +1,4 @@
-"""Eigenvalue adjoint (a12) on the GPU against the oracle's adjoint and, through the
+"""Eigenvalue adjoint on the GPU against the oracle's adjoint and, through the
 autograd wrapper, against finite differences of whole GPU solves."""
 import numpy as np
 import pytest

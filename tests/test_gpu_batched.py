@@ -1,4 +1,4 @@
-"""Batched uneven pencils (a11): several independent problems of different families and
+"""Batched uneven pencils: several independent problems of different families and
 sizes solved in one batch, whose COCG phases run as one persistent launch.
 
 Checks: every problem's eigenvalues against a dense generalized eigensolver (count

@@ -13,7 +13,7 @@ COCG amplifies rounding more; the CSR path measured 1.18e-8 there at It_max 9).
 
 B-diagonal records (slrf_opts.bdiag): bitwise equal to the general records (exact zeros).
 
-Jacobi preconditioner (slrf_opts.precond, reading R18): compared with the oracle's
+Jacobi preconditioner (slrf_opts.precond, D = diag(A) applied on both sides): compared with the oracle's
 preconditioned COCG on the same scaled systems (D = diag(A)); the tolerances are those of
 the unpreconditioned parity tests (U to 1e-8 of max |U|, update counts identical).
 """

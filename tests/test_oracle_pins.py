@@ -22,7 +22,7 @@ def _small_q1(nodes=(6, 5, 4), shift=1e-3):
     return p, p.A(), p.B()
 
 
-# ---------------------------------------------------------------- a1: poles and weights
+# ---------------------------------------------------------------- poles and weights
 def test_poles_on_shifted_laplace_line():
     """Sec. 2.2: sigma = Re(sigma) (1 + alpha i); real parts inside (0, gamma)."""
     for alpha in (1.0, 0.5):
@@ -58,7 +58,8 @@ def test_pole_weights_solve_the_regularised_fit():
 
 def test_filter_shape():
     """Phi passes (0, gamma] and damps [1.3 gamma, inf): the filter property of Sec. 2.
-    The design (reading R1, m = 8, alpha = 1, beta = 0.01) has, on the normalised axis,
+    The design (midpoint abscissae, Tikhonov-regularised fit; m = 8, alpha = 1, beta = 0.01)
+    has, on the normalised axis,
     min Phi = 0.8711 (at t = gamma), max Phi = 1.0400 (at t = 0.832 gamma) on (0, gamma],
     max |Phi| = 0.2233 beyond 1.3 gamma (at the band edge) and 0.0885 beyond 1.4 gamma."""
     g = 4150.528
@@ -77,7 +78,7 @@ def test_filter_shape():
     assert abs(full.imag) < 1e-12 and abs(full.real - orc.filter_value(t, s, w)) < 1e-12
 
 
-# ---------------------------------------------------------------- a3/a4: COCG
+# ---------------------------------------------------------------- COCG
 def test_cocg_equals_scipy_cg_for_a_real_shift():
     """For a real shift sigma < 0, A - sigma B is SPD and COCG is CG: iterate k matches
     scipy's CG stopped after k iterations."""
@@ -150,7 +151,7 @@ def _galerkin_iterate(M, r0, k):
 
 @pytest.mark.parametrize("precond", [False, True])
 def test_cocg_iterates_satisfy_the_galerkin_condition(precond):
-    """COCG (and its Jacobi-preconditioned form, reading R18) after k steps equals the
+    """COCG (and its Jacobi-preconditioned form) after k steps equals the
     Petrov-Galerkin iterate of the (scaled) system in the Krylov space of its initial
     residual, from a nonzero initial guess.  Preconditioned: the system is
     D^-1/2 (A - sigma B) D^-1/2 z = D^-1/2 b with D = diag(A), z = D^1/2 y."""
@@ -195,7 +196,7 @@ def test_preconditioned_cocg_solves_the_unscaled_system():
     assert np.allclose(i1.relres, i2.relres, rtol=1e-10)
 
 
-# ---------------------------------------------------------------- a5: the filter on eigenvectors
+# ---------------------------------------------------------------- the filter on eigenvectors
 def test_filter_apply_on_exact_eigenvectors():
     """With X exact eigenvectors and converged solves, filter_apply(X) = X diag(Phi(lambda))."""
     p, A, B = _small_q1((5, 4, 3))
@@ -264,7 +265,7 @@ def test_ritz_residuals_closed_form():
 
 
 def test_sign_normalise():
-    """Reading R11: each vector's entry of largest magnitude is made positive; among equal
+    """Sign convention: each vector's entry of largest magnitude is made positive; among equal
     magnitudes the first one decides; a zero vector stays zero."""
     V = np.array([[1.0, 2.0, 0.0, -0.5],
                   [-3.0, -2.0, 0.0, 0.25],
@@ -360,7 +361,7 @@ def test_stop_rule_needs_a_resolved_subspace():
 
 
 def test_preconditioned_solve_against_dense_eigh():
-    """Alg. 2 with Jacobi-preconditioned inner solves (reading R18) returns the same
+    """Alg. 2 with Jacobi-preconditioned inner solves returns the same
     eigenpairs: the preconditioner changes how fast, not what, the method converges to."""
     E = np.exp(np.random.default_rng(9).normal(0, 0.5, 3 * 3 * 2))
     p = si.q1_elasticity((4, 4, 3), E=E)
@@ -399,7 +400,7 @@ def test_sturm_count_matches_dense():
         assert c == pins.dense_inertia_count(p.A(), p.B(), gamma) == np.sum(pins.bar1d_eigs(n) < gamma)
 
 
-# ---------------------------------------------------------------- a12: eigenvalue adjoint
+# ---------------------------------------------------------------- eigenvalue adjoint
 def test_eig_grad_matches_finite_differences():
     """Central differences of the dense generalized eigenvalues along random symmetric
     directions on the pattern match the adjoint, for A and for B."""
@@ -430,7 +431,7 @@ def test_eig_grad_matches_finite_differences():
             assert abs(fd - pred) <= 1e-5 * abs(fd), (other, fd, pred)
 
 
-# ---------------------------------------------------------------- a13: eigenvector adjoint
+# ---------------------------------------------------------------- eigenvector adjoint
 def _eig_sorted(Ad, Bd, k):
     lam, X = sla.eigh(Ad, Bd)
     X = X[:, :k]
